@@ -314,12 +314,8 @@ static void heap_swap(orc_state* st, int i, int j) {
   st->heap[i] = b; st->heap[j] = a;
   st->hpos[b] = i; st->hpos[a] = j;
 }
-static void heap_fix(orc_state* st, int i) {
+static void heap_sift_down(orc_state* st, int i) {
   int n = st->nreg;
-  while (i > 0 && heap_less(st, st->heap[i], st->heap[(i - 1) / 2])) {
-    heap_swap(st, i, (i - 1) / 2);
-    i = (i - 1) / 2;
-  }
   for (;;) {
     int l = 2 * i + 1, r = l + 1, m = i;
     if (l < n && heap_less(st, st->heap[l], st->heap[m])) m = l;
@@ -328,6 +324,14 @@ static void heap_fix(orc_state* st, int i) {
     heap_swap(st, i, m);
     i = m;
   }
+}
+/* Restore the heap after the key of the entry at position i changed. */
+static void heap_fix(orc_state* st, int i) {
+  while (i > 0 && heap_less(st, st->heap[i], st->heap[(i - 1) / 2])) {
+    heap_swap(st, i, (i - 1) / 2);
+    i = (i - 1) / 2;
+  }
+  heap_sift_down(st, i);
 }
 
 /* Site of class k whose 0-based row-major rank among class-k sites of region r is pos (R6). */
@@ -486,7 +490,7 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
     st.heap[r] = r;
     st.hpos[r] = r;
   }
-  for (int i = st.nreg / 2; i >= 0; i--) heap_fix(&st, i);
+  for (int i = st.nreg / 2; i >= 0; i--) heap_sift_down(&st, i);   /* bottom-up heap build */
   out->trace_len = 0;
   out->debug_failures = 0;
   if (prm->debug) out->debug_failures += count_debug(&st);
