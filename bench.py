@@ -1,0 +1,330 @@
+"""Benchmark: committed spin flips per second of the synchronous-relaxation
+n-fold-way Ising simulation on GB300.
+
+Workload (one "step" = the whole hot path over the lattice, for each window
+length): L = 1024 periodic 2D Ising, 64 x 64 regions of 16 x 16, J = 1,
+h = 0.05, T = 1.0, fair-coin initial spins from the seed; for each window
+length Tw in {0.25, 1, 4}: initialise (spins, class counts, first waiting
+times), run synchronous relaxation windows to t = 100, reduce the observables.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 is launched with torch.distributed.run: each rank simulates its own
+replica (seed 1 + rank) on its own GPU, with no data exchange ("scaling":
+"weak"); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "committed spin flips/s on 1 GB300 (batched vs plain), % roofline, iters"
+UNIT = "flips/s"
+L, RW, RH, J, H_FIELD, TEMP, T_END = 1024, 16, 16, 1.0, 0.05, 1.0, 100.0
+WINDOWS = (0.25, 1.0, 4.0)
+WORKLOAD = ("L=1024 periodic 2D Ising, 64x64 regions of 16x16, J=1, h=0.05, T=1.0, fair-coin "
+            "spins, Metropolis rates via the n-fold way, run to t=100 for each window length "
+            "Tw in {0.25, 1, 4}")
+
+# FP64 pipe operations per committed event and per break point of the method
+# as formulated here (counted from the formulas; divisions counted in the
+# FP64-pipe slots one IEEE division takes on this part, measured 8.6).
+FP64_DIV_SLOTS = 8.6
+FP64_PER_EVENT = 28 + 2 * FP64_DIV_SLOTS + 8      # -log U (Horner, scale, ln2), tau, observables
+FP64_PER_BREAK = 6 + FP64_DIV_SLOTS               # accrual, new tau
+FP64_PEAK_OPS = 5.0e11                            # measured DFMA/DADD lane-ops/s, all 152 SMs
+HIST_BYTES_PER_BOUNDARY_EVENT = 9 * 2             # f64 time + u8 position, written once, read once
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None
+
+
+def _clock_summary(path, gpu_index):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def _oracle_baseline(steps_for_ref=None):
+    """The oracle (plain sequential C) on the same workload: one run covers all
+    three window lengths, since window ends do not change its trajectory."""
+    import oracle
+    oracle.build()
+    ends = [float(t) for t in range(1, int(T_END) + 1)]
+    t0 = time.perf_counter()
+    r = oracle.run(L, J, H_FIELD, TEMP, RW, RH, 1, ends, keep_spins=False)
+    dt = time.perf_counter() - t0
+    committed = int(r.counts[-1].sum())
+    return committed, dt
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        _oracle_baseline()
+    times, committed = [], 0
+    for _ in range(args.steps):
+        c, dt = _oracle_baseline()
+        committed += c * len(WINDOWS)
+        times.append(dt)
+    total = sum(times)
+    value = committed / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "the full workload: one oracle run to t=100 per step stands for "
+                                   "all three window lengths (its trajectory does not depend on "
+                                   "window ends); counted three times per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_cs_0405053_gb300 as sr
+
+    rank, world, local = _dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    seed = 1 + rank
+    stream = torch.cuda.current_stream()
+    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def one_pass(record):
+        """One step: for each window length, init + windows to t=100 + observables."""
+        out = []
+        for Tw in WINDOWS:
+            n = int(round(T_END / Tw))
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            lat.reset()
+            ev[1].record(stream)
+            lat.run_windows(Tw, n)
+            ev[2].record(stream)
+            obs = lat.observables()
+            ev[3].record(stream)
+            out.append((Tw, ev, obs, lat.window_iters(n)))
+        return out
+
+    for _ in range(args.warmup):
+        one_pass(False)
+    torch.cuda.synchronize()
+
+    clock_path = os.path.join(tempfile.gettempdir(), f"sr_clocks_{os.getpid()}.csv")
+    sampler = _clock_sampler(clock_path) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    step_ms, kernel_ms, per_tw = [], [], {Tw: [] for Tw in WINDOWS}
+    committed_total = 0
+    launches0 = lat.observables().launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()                         # L2 flush between timed steps (outside the events)
+        res = one_pass(True)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for Tw, ev, obs, iters in res:
+            ms += ev[0].elapsed_time(ev[3])
+            kernel_ms.append(ev[1].elapsed_time(ev[2]))
+            committed_total += obs.committed          # counters restart at each reset
+            launches_last = obs.launches
+            per_tw[Tw].append((ev[0].elapsed_time(ev[3]), ev[1].elapsed_time(ev[2]), obs, iters))
+        step_ms.append(ms)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    launches = launches_last - launches0
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    total_ms = sum(step_ms)
+    t_dev = torch.tensor([total_ms / 1e3], dtype=torch.float64, device="cuda")
+    c_dev = torch.tensor([float(committed_total)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c_dev, op=dist.ReduceOp.SUM)
+    t_max = float(t_dev.item())
+    value = float(c_dev.item()) / t_max
+
+    # ---- end to end through the public API with host buffers: upload the
+    # initial spins from pinned memory, run, read back observables and spins
+    rng = np.random.default_rng(1000 + rank)
+    init_host = torch.from_numpy(np.where(rng.random((L, L)) < 0.5, 1, -1).astype(np.int8)).pin_memory()
+    out_host = torch.empty((L, L), dtype=torch.int8).pin_memory()
+    e2e_lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed)
+    e2e_committed, e2e_time = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        c_step = 0
+        for Tw in WINDOWS:
+            e2e_lat.set_spins(init_host.numpy())
+            e2e_lat.run_windows(Tw, int(round(T_END / Tw)))
+            o = e2e_lat.observables()
+            sr.library().sr_get_spins(e2e_lat._ctx, out_host.data_ptr(), L * L)
+            c_step += o.committed
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            e2e_committed += c_step
+            e2e_time += dt
+    e2e_lat.close()
+    e2e_value = e2e_committed / e2e_time if e2e_time > 0 else None
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (the persistent relaxation kernel)
+    kms = sum(kernel_ms) / len(kernel_ms)
+    last = {Tw: per_tw[Tw][-1] for Tw in WINDOWS}
+    ev_per_launch = statistics.mean(o.committed for (_, _, o, _) in (last[t] for t in WINDOWS))
+    brk_per_launch = statistics.mean(o.breaks / max(1, o.iterations) * o.last_iters
+                                     for (_, _, o, _) in (last[t] for t in WINDOWS))
+    fp64_ops = ev_per_launch * FP64_PER_EVENT
+    achieved = fp64_ops / (kms * 1e-3)
+    peak = FP64_PEAK_OPS
+    cpu_committed, cpu_dt = _oracle_baseline()
+    tw_detail = {}
+    for Tw in WINDOWS:
+        ms, kms_tw, o, iters = per_tw[Tw][-1]
+        it = [int(v) for v in iters]
+        tw_detail[str(Tw)] = {
+            "ms": round(ms, 3), "kernel_ms": round(kms_tw, 3), "committed": o.committed,
+            "generated": o.generated, "wasted_ratio": (o.generated - o.committed) / max(1, o.committed),
+            "iters_mean": statistics.mean(it) if it else None, "iters_max": max(it) if it else None,
+            "windows": len(it), "max_f": o.max_f, "breaks": o.breaks,
+            "flips_per_s": o.committed / (ms * 1e-3)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded fair-coin lattice)",
+        "config": {"workload": WORKLOAD, "regions": lat.n_regions,
+                   "launch": {"threads_per_block": lat.threads_per_block, "blocks": lat.blocks},
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "per_window_length": tw_detail},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "pipe": "FP64 (measured DFMA/DADD rate of this part)",
+                     "kernel": "relax_kernel", "kernel_ms_avg": kms,
+                     "fp64_ops_per_committed_event": FP64_PER_EVENT},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": L * L * len(WINDOWS),
+                "d2h_bytes_per_step": (L * L + 64) * len(WINDOWS)},
+        "gpu_launches": launches,
+        "cpu_baseline": {"value": cpu_committed / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "full workload trajectory to t=100 (one run; the oracle's "
+                                   "trajectory does not depend on window ends)"},
+        "clocks": _clock_summary(clock_path, local),
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_case(args):
+    """A short slice of the workload for profilers: the L=1024 lattice from
+    t = 0 through `--windows` windows of length `--tw` (one persistent launch)."""
+    import torch
+
+    import paper_cs_0405053_gb300 as sr
+    torch.cuda.set_device(0)
+    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=1)
+    for _ in range(args.warmup):
+        lat.reset()
+        lat.run_windows(args.tw, args.windows)
+    lat.reset()
+    lat.run_windows(args.tw, args.windows)
+    o = lat.observables()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": True, "tw": args.tw, "windows": args.windows,
+                      "committed": o.committed, "generated": o.generated,
+                      "iterations": o.iterations}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run only a short slice of the workload (for ncu)")
+    ap.add_argument("--tw", type=float, default=1.0)
+    ap.add_argument("--windows", type=int, default=5)
+    args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

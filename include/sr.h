@@ -1,0 +1,196 @@
+/*
+ * sr.h -- C ABI of libsr: synchronous relaxation of the continuous-time
+ * n-fold-way Ising simulation (Lubachevsky & Weiss, "Synchronous Relaxation
+ * for Parallel Ising Spin Simulations"), GPU implementation for sm_103a.
+ *
+ * The lattice G (§2) is an L x L periodic square lattice of spins s = +-1,
+ * partitioned into rectangular regions G_i of region_w x region_h sites
+ * (§5: "The set G is partitioned into subsets G_i").  Each region plays the
+ * part of one processing element of §4: it generates its own n-fold-way history
+ * (§3) over a window [t_c, t_c + T_max), reading its neighbours' boundary
+ * histories from the previous iteration; the iterations repeat until no
+ * boundary history changes (§4, boxed procedure; §5).
+ *
+ * Conventions shared by every call:
+ *   - Return value: SR_OK (0) on success, a negative SR_E* code otherwise.
+ *     No call throws.  sr_strerror() names a code.
+ *   - The library owns every device buffer it allocates; the caller owns every
+ *     buffer it passes in (host memory unless the name ends in _device).
+ *   - A context is not thread-safe.  All GPU work of a context runs on the
+ *     stream given at creation (or a stream the library creates).
+ *   - Spin arrays are int8, row-major, index y * L + x, values +1 / -1.
+ *   - Region r covers x in [rx*region_w, (rx+1)*region_w) and y in
+ *     [ry*region_h, (ry+1)*region_h) with r = ry * (L / region_w) + rx.
+ */
+#ifndef SR_H
+#define SR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SR_OK 0
+#define SR_EINVAL (-1)          /* bad argument (shape, L < 3, T <= 0, t0 != committed time ...) */
+#define SR_ENOMEM (-2)          /* device or host allocation failed */
+#define SR_ECUDA (-3)           /* a CUDA call failed */
+#define SR_NOT_CONVERGED (-4)   /* iteration cap reached before a fixed point (§4, "UNTIL") */
+#define SR_CAPACITY (-5)        /* boundary history larger than the largest allowed capacity */
+#define SR_TIMEOUT (-6)         /* a grid-wide synchronize waited longer than its limit */
+#define SR_EUNSUPPORTED (-7)    /* valid but not supported by this build (e.g. region wider than 32) */
+
+/* ---- initial spins ---- */
+#define SR_INIT_FAIR_COIN 0     /* bit 0 of Philox4x32-10(counter = (site, 0, 0, 1), key = seed) */
+#define SR_INIT_ALL_UP 1
+#define SR_INIT_ALL_DOWN 2
+
+/* ---- flip probability p (§2) ---- */
+#define SR_RATES_METROPOLIS 0   /* p = min(1, theta), Eq. 2.2 */
+#define SR_RATES_GLAUBER 1      /* p = theta / (1 + theta), Eq. 2.3 */
+
+typedef struct sr_ctx sr_ctx;   /* opaque, library-owned */
+
+/* Creation parameters.  Zero-initialise and set what you need. */
+typedef struct sr_params {
+  int L;                        /* lattice side, >= 3 (§2, periodic in both directions) */
+  double J;                     /* coupling of Eq. 2.1 (each nearest-neighbour bond counted once) */
+  double h;                     /* field H of Eq. 2.1 */
+  double T;                     /* temperature k_B T_abs of Eq. 2.2, > 0 */
+  int region_w, region_h;       /* region extent in x and y; must divide L; each <= 32 */
+  uint64_t seed;                /* key of every random stream */
+  int init_mode;                /* SR_INIT_* */
+  int rates;                    /* SR_RATES_* */
+  int capacity;                 /* boundary events per region edge per iteration; 0 = automatic
+                                   (grows by doubling when exceeded, see sr_run_windows) */
+  int max_iters;                /* iteration cap per window; 0 = 1<<16 */
+  int trace_capacity;           /* committed events recorded per region; 0 = no trace */
+  int threads_per_block;        /* region lanes per block (one region per lane); 0 = automatic */
+  int block_threads;            /* threads per block, >= region lanes; the extra threads help
+                                   draw the presimulated random pairs; 0 = automatic */
+  int blocks;                   /* 0 = automatic (all regions resident if they fit) */
+  int barrier_timeout_ms;       /* bound on each grid-wide wait; 0 = 2000 */
+  int test_barrier_skip_block;  /* test hook: this block never arrives at a barrier; -1 = off */
+  void* stream;                 /* cudaStream_t; NULL = the library creates its own */
+} sr_params;
+
+/* Observables and counters (reduced over all regions at the committed time). */
+typedef struct sr_obs {
+  double t_c;                   /* committed time (§4) */
+  int64_t mag;                  /* sum of spins */
+  int64_t bonds;                /* sum over nearest-neighbour bonds of s s' */
+  double m;                     /* mag / L^2 */
+  double E;                     /* -J bonds - h mag (Eq. 2.1) */
+  double int_mag;               /* integral of mag dt over [0, t_c] */
+  double int_bonds;             /* integral of bonds dt over [0, t_c] */
+  uint64_t committed;           /* committed events since creation */
+  uint64_t generated;           /* events generated in every iteration (committed or discarded) */
+  uint64_t breaks;              /* break points processed in every iteration (§5) */
+  uint64_t windows;             /* committed windows */
+  uint64_t iterations;          /* iterations over all windows */
+  uint32_t last_iters;          /* iterations of the last window (g of §6) */
+  uint32_t max_iters_seen;      /* largest g seen */
+  uint32_t max_f;               /* largest number of boundary events of one region in one
+                                   iteration (f of §6) */
+  uint32_t capacity;            /* current history capacity per edge */
+  uint64_t launches;            /* kernels this context has launched since creation */
+} sr_obs;
+
+/* Create a context with Metropolis rates, fair-coin initial spins and
+ * automatic settings.  Computes p_k for the ten classes k = 5*[s=+1] + n_up
+ * (§3, Eqs. 3.1-3.2), allocates the device state, initialises the spins, the
+ * class counts N_k and every region's first waiting time (Eq. 3.4 with
+ * tau_0 = 0, §5 "First iteration, first step"); committed time t_c = 0.
+ * *out receives the handle (NULL on failure).  Errors: SR_EINVAL, SR_ENOMEM,
+ * SR_ECUDA, SR_EUNSUPPORTED. */
+int sr_create(sr_ctx** out, int L, double J, double h, double T, int region_w, int region_h,
+              uint64_t seed);
+
+/* Same as sr_create with every setting of sr_params. */
+int sr_create_ex(sr_ctx** out, const sr_params* params);
+
+/* One step of the §4 procedure with T_max = Tw: make the canonical assumption
+ * (no neighbour flips, §5), iterate "generate / synchronize / compare /
+ * synchronize" until no region's boundary history changes, then increment the
+ * committed time by Tw.  t0 must equal the committed time.  Blocks until the
+ * window is done.  Errors: SR_EINVAL (t0 != t_c, Tw <= 0), SR_NOT_CONVERGED,
+ * SR_CAPACITY, SR_TIMEOUT, SR_ECUDA.  On error the committed state is that of
+ * the last window that converged. */
+int sr_run_window(sr_ctx* ctx, double t0, double Tw);
+
+/* n consecutive windows of length Tw from t0 (= t_c), in one persistent
+ * launch; window k ends at the double t0 + Tw + ... + Tw (k+1 additions).
+ * When a window overflows the history capacity and capacity was automatic,
+ * the capacity is doubled and the remaining windows are re-run from the last
+ * committed state (the result does not depend on the capacity).  Same errors as
+ * sr_run_window. */
+int sr_run_windows(sr_ctx* ctx, double t0, double Tw, int n);
+
+/* Observables at the committed time; *out is caller-owned.  Errors: SR_EINVAL,
+ * SR_ECUDA. */
+int sr_observables(sr_ctx* ctx, sr_obs* out);
+
+/* Free everything; NULL-safe. */
+void sr_destroy(sr_ctx* ctx);
+
+/* Copy the committed spins into a caller buffer of n = L*L int8.  Errors:
+ * SR_EINVAL (n != L*L), SR_ECUDA. */
+int sr_get_spins(sr_ctx* ctx, int8_t* host_out, size_t n);
+
+/* Same into a device buffer (caller-owned, n = L*L bytes); ordered on the
+ * context's stream, returns without waiting. */
+int sr_get_spins_device(sr_ctx* ctx, int8_t* dev_out, size_t n);
+
+/* Restart from a given configuration: spins > 0 are up, others down; t_c = 0
+ * and every region's clock restarts as at creation (event index 0, tau_0 = 0).
+ * Counters are cleared.  Errors: SR_EINVAL (n != L*L), SR_ECUDA. */
+int sr_set_spins(sr_ctx* ctx, const int8_t* host_in, size_t n);
+
+/* Same from a device buffer; ordered on the context's stream. */
+int sr_set_spins_device(sr_ctx* ctx, const int8_t* dev_in, size_t n);
+
+/* Back to the creation-time initial state (t_c = 0, counters cleared). */
+int sr_reset(sr_ctx* ctx);
+
+/* Per-region clock state at t_c (§5, "Subsequent steps"): index i of the
+ * pending event, x = -log U_i, b = integral of Lambda since the last event up
+ * to time t_last.  Arrays of n = number of regions; any may be NULL.  The
+ * event index equals the number of committed events of the region. */
+int sr_get_carry(sr_ctx* ctx, uint64_t* index, double* x, double* b, double* t_last, size_t n);
+
+/* Committed events of every region in order (requires trace_capacity > 0):
+ * lens[r] = number of committed events of region r (entries beyond
+ * trace_capacity were not recorded); times[r * cap + j], sites[r * cap + j]
+ * (site = y * L + x) for j < min(lens[r], cap), cap = trace_capacity.  Any
+ * pointer may be NULL. */
+int sr_get_trace(sr_ctx* ctx, uint64_t* lens, double* times, uint32_t* sites, size_t n_regions,
+                 size_t cap);
+
+/* Iteration count g of each of the last n windows run by the last
+ * sr_run_window(s) call (at most 4096); returns how many were written or a
+ * negative code. */
+int sr_get_window_iters(sr_ctx* ctx, uint32_t* out, size_t n);
+
+/* Geometry and the fixed-point rate table actually used: P[k] / 2^F is the
+ * flip probability of class k (the grid keeps Lambda = sum N_k p_k exact);
+ * threads_per_block receives the region lanes per block.  Any pointer may be
+ * NULL. */
+int sr_get_info(sr_ctx* ctx, int* n_regions, int* frac_bits, uint64_t* P, int* threads_per_block,
+                int* blocks);
+
+/* Evaluate on the GPU the random pairs of events i0 .. i0+n-1 of one region:
+ * x[j] = -log U_i (the numerator of Eq. 3.4) and kV[j], the 52-bit integer of
+ * V_i = (2 kV + 1) 2^-53 (Phase 1 of §3), for counter (i, region) under seed.
+ * Host arrays of n entries; either may be NULL.  Blocks until done.  Errors:
+ * SR_EINVAL, SR_ENOMEM, SR_ECUDA. */
+int sr_eval_draws(uint64_t seed, uint32_t region, uint64_t i0, size_t n, double* x, uint64_t* kV);
+
+/* Name of a status code (static string). */
+const char* sr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SR_H */

@@ -1,0 +1,268 @@
+"""GB300 (sm_103a) synchronous relaxation of the continuous-time n-fold-way
+Ising simulation (Lubachevsky & Weiss, "Synchronous Relaxation for Parallel
+Ising Spin Simulations").
+
+This module is a thin ctypes binding of ``libsr`` (C ABI in ``include/sr.h``);
+every step of the simulation runs in the library's CUDA kernels.  PyTorch, when
+present, only supplies the CUDA stream and device buffers.  There is no CPU
+fallback: without the compiled library or a GPU every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["SRError", "Lattice", "Observables", "library", "eval_draws", "SR_OK"]
+
+SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA = 0, -1, -2, -3
+SR_NOT_CONVERGED, SR_CAPACITY, SR_TIMEOUT, SR_EUNSUPPORTED = -4, -5, -6, -7
+INIT_MODES = {"fair": 0, "up": 1, "down": 2}
+RATES = {"metropolis": 0, "glauber": 1}
+
+
+class SRError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {library().sr_strerror(code).decode()} ({code})")
+
+
+class _Params(C.Structure):
+    _fields_ = [("L", C.c_int), ("J", C.c_double), ("h", C.c_double), ("T", C.c_double),
+                ("region_w", C.c_int), ("region_h", C.c_int), ("seed", C.c_uint64),
+                ("init_mode", C.c_int), ("rates", C.c_int), ("capacity", C.c_int),
+                ("max_iters", C.c_int), ("trace_capacity", C.c_int),
+                ("threads_per_block", C.c_int), ("block_threads", C.c_int), ("blocks", C.c_int),
+                ("barrier_timeout_ms", C.c_int), ("test_barrier_skip_block", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class _Obs(C.Structure):
+    _fields_ = [("t_c", C.c_double), ("mag", C.c_int64), ("bonds", C.c_int64), ("m", C.c_double),
+                ("E", C.c_double), ("int_mag", C.c_double), ("int_bonds", C.c_double),
+                ("committed", C.c_uint64), ("generated", C.c_uint64), ("breaks", C.c_uint64),
+                ("windows", C.c_uint64), ("iterations", C.c_uint64), ("last_iters", C.c_uint32),
+                ("max_iters_seen", C.c_uint32), ("max_f", C.c_uint32), ("capacity", C.c_uint32),
+                ("launches", C.c_uint64)]
+
+
+@dataclass
+class Observables:
+    t_c: float
+    mag: int
+    bonds: int
+    m: float
+    E: float
+    int_mag: float
+    int_bonds: float
+    committed: int
+    generated: int
+    breaks: int
+    windows: int
+    iterations: int
+    last_iters: int
+    max_iters_seen: int
+    max_f: int
+    capacity: int
+    launches: int
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def library(build_if_missing: bool = True) -> C.CDLL:
+    """Load libsr (building it in-tree first when the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing and _build.stale():
+            _build.build()
+        if not os.path.exists(path):
+            raise OSError(f"libsr is not built: {path} is missing (run __graft_entry__.build())")
+        lib = C.CDLL(path)
+        sig = {
+            "sr_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_double, C.c_double, C.c_double,
+                                    C.c_int, C.c_int, C.c_uint64]),
+            "sr_create_ex": (C.c_int, [C.POINTER(_P), C.POINTER(_Params)]),
+            "sr_run_window": (C.c_int, [_P, C.c_double, C.c_double]),
+            "sr_run_windows": (C.c_int, [_P, C.c_double, C.c_double, C.c_int]),
+            "sr_observables": (C.c_int, [_P, C.POINTER(_Obs)]),
+            "sr_destroy": (None, [_P]),
+            "sr_get_spins": (C.c_int, [_P, _P, C.c_size_t]),
+            "sr_get_spins_device": (C.c_int, [_P, _P, C.c_size_t]),
+            "sr_set_spins": (C.c_int, [_P, _P, C.c_size_t]),
+            "sr_set_spins_device": (C.c_int, [_P, _P, C.c_size_t]),
+            "sr_reset": (C.c_int, [_P]),
+            "sr_get_carry": (C.c_int, [_P, _P, _P, _P, _P, C.c_size_t]),
+            "sr_get_trace": (C.c_int, [_P, _P, _P, _P, C.c_size_t, C.c_size_t]),
+            "sr_get_window_iters": (C.c_int, [_P, _P, C.c_size_t]),
+            "sr_eval_draws": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint64, C.c_size_t, _P, _P]),
+            "sr_get_info": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+            "sr_strerror": (C.c_char_p, [C.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(code: int, what: str) -> None:
+    if code != SR_OK:
+        raise SRError(code, what)
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+def _torch_stream():
+    try:
+        import torch
+    except ImportError:       # the library creates its own stream
+        return None
+    if not torch.cuda.is_available():
+        return None
+    return torch.cuda.current_stream().cuda_stream
+
+
+def eval_draws(seed: int, region: int, i0: int, n: int) -> Tuple[np.ndarray, np.ndarray]:
+    """(x = -log U_i, kV_i) for events i0 .. i0+n-1 of a region, on the GPU."""
+    x = np.zeros(n, dtype=np.float64)
+    kv = np.zeros(n, dtype=np.uint64)
+    _check(library().sr_eval_draws(seed, region, i0, n, _ptr(x), _ptr(kv)), "sr_eval_draws")
+    return x, kv
+
+
+class Lattice:
+    """One L x L periodic lattice split into region_w x region_h regions."""
+
+    def __init__(self, L: int, J: float = 1.0, h: float = 0.0, T: float = 1.0,
+                 region: Tuple[int, int] = (16, 16), seed: int = 1, init: str = "fair",
+                 rates: str = "metropolis", capacity: int = 0, max_iters: int = 0,
+                 trace_capacity: int = 0, threads_per_block: int = 0, block_threads: int = 0,
+                 blocks: int = 0,
+                 barrier_timeout_ms: int = 0, test_barrier_skip_block: int = -1,
+                 stream: Optional[int] = None, use_torch_stream: bool = True):
+        lib = library()
+        if stream is None and use_torch_stream:
+            stream = _torch_stream()
+        self.L, self.J, self.h, self.T = L, J, h, T
+        self.region = region
+        self.seed = seed
+        self.trace_capacity = trace_capacity
+        prm = _Params(L, J, h, T, region[0], region[1], seed, INIT_MODES[init], RATES[rates],
+                      capacity, max_iters, trace_capacity, threads_per_block, block_threads, blocks,
+                      barrier_timeout_ms, test_barrier_skip_block, stream)
+        self._ctx = _P()
+        _check(lib.sr_create_ex(C.byref(self._ctx), C.byref(prm)), "sr_create_ex")
+        n_regions = C.c_int()
+        frac = C.c_int()
+        tpb = C.c_int()
+        blk = C.c_int()
+        P = np.zeros(10, dtype=np.uint64)
+        _check(lib.sr_get_info(self._ctx, C.byref(n_regions), C.byref(frac), _ptr(P), C.byref(tpb),
+                               C.byref(blk)), "sr_get_info")
+        self.n_regions = n_regions.value
+        self.frac_bits = frac.value
+        self.P = P
+        self.threads_per_block = tpb.value
+        self.blocks = blk.value
+        self.t_c = 0.0
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            library().sr_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the method
+    def run_window(self, Tw: float) -> None:
+        """One synchronous-relaxation step of length Tw from the committed time."""
+        code = library().sr_run_window(self._ctx, self.t_c, Tw)
+        self.t_c = self.t_c + Tw if code == SR_OK else self.observables().t_c
+        _check(code, "sr_run_window")
+
+    def run_windows(self, Tw: float, n: int) -> None:
+        code = library().sr_run_windows(self._ctx, self.t_c, Tw, n)
+        if code == SR_OK:
+            for _ in range(n):
+                self.t_c = self.t_c + Tw
+        else:
+            self.t_c = self.observables().t_c
+        _check(code, "sr_run_windows")
+
+    def observables(self) -> Observables:
+        o = _Obs()
+        _check(library().sr_observables(self._ctx, C.byref(o)), "sr_observables")
+        return Observables(*[getattr(o, f) for f, _ in _Obs._fields_])
+
+    def spins(self) -> np.ndarray:
+        out = np.zeros((self.L, self.L), dtype=np.int8)
+        _check(library().sr_get_spins(self._ctx, _ptr(out), out.size), "sr_get_spins")
+        return out
+
+    def spins_into(self, dev_ptr: int) -> None:
+        """Unpack the committed spins into a caller-owned device buffer of L*L int8."""
+        _check(library().sr_get_spins_device(self._ctx, dev_ptr, self.L * self.L),
+               "sr_get_spins_device")
+
+    def set_spins(self, spins: np.ndarray) -> None:
+        a = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
+        _check(library().sr_set_spins(self._ctx, _ptr(a), a.size), "sr_set_spins")
+        self.t_c = 0.0
+
+    def set_spins_from(self, dev_ptr: int) -> None:
+        _check(library().sr_set_spins_device(self._ctx, dev_ptr, self.L * self.L),
+               "sr_set_spins_device")
+        self.t_c = 0.0
+
+    def reset(self) -> None:
+        _check(library().sr_reset(self._ctx), "sr_reset")
+        self.t_c = 0.0
+
+    def carry(self):
+        n = self.n_regions
+        i = np.zeros(n, dtype=np.uint64)
+        x = np.zeros(n, dtype=np.float64)
+        b = np.zeros(n, dtype=np.float64)
+        t = np.zeros(n, dtype=np.float64)
+        _check(library().sr_get_carry(self._ctx, _ptr(i), _ptr(x), _ptr(b), _ptr(t), n),
+               "sr_get_carry")
+        return i, x, b, t
+
+    def trace(self):
+        """(lens[n_regions], times[n_regions, cap], sites[n_regions, cap])."""
+        n, cap = self.n_regions, self.trace_capacity
+        lens = np.zeros(n, dtype=np.uint64)
+        times = np.zeros((n, cap), dtype=np.float64)
+        sites = np.zeros((n, cap), dtype=np.uint32)
+        _check(library().sr_get_trace(self._ctx, _ptr(lens), _ptr(times), _ptr(sites), n, cap),
+               "sr_get_trace")
+        return lens, times, sites
+
+    def window_iters(self, n: int = 4096) -> np.ndarray:
+        out = np.zeros(n, dtype=np.uint32)
+        m = library().sr_get_window_iters(self._ctx, _ptr(out), n)
+        if m < 0:
+            raise SRError(m, "sr_get_window_iters")
+        return out[:m]

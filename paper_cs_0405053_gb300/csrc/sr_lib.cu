@@ -1,0 +1,1349 @@
+// sr_lib.cu -- libsr: synchronous relaxation of the continuous-time n-fold-way
+// Ising simulation on one GPU (sm_103a).  C ABI in include/sr.h.
+//
+// Mapping (Lubachevsky & Weiss, §4-§5):
+//   * A region G_i is one lane ("PE").  Its spins live bit-packed in shared
+//     memory, one 32-bit word per row; its ten class counts N_k (§3) in
+//     shared memory; the total rate Lambda = sum_k N_k p_k (Eq. 3.3) as an
+//     exact integer on the 2^-F grid.  One lane per region keeps every FP64
+//     instruction 32 regions wide, the only way to use the FP64 pipe well on
+//     this part: a warp-wide FP64 instruction costs the same whatever the
+//     number of active lanes.
+//   * "Synchronize" (§4 boxed procedure) is a grid-wide barrier of a persistent
+//     cooperative kernel; "all PEs detect no difference" is a grid flag set by
+//     atomics.  Every wait is bounded and ends in SR_TIMEOUT, never a hang.
+//   * Boundary histories (§5, "the single layer of atoms that border its
+//     region") are per-edge lists of (time, position) in HBM, double-buffered by
+//     iteration parity: iteration n reads the neighbours' lists of iteration
+//     n-1 (§4: "uses that history generated in the last iteration") and
+//     compares its own new lists with its own previous ones.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "sr.h"
+#include "sr_device.cuh"
+
+namespace sr {
+
+enum : unsigned { ST_CAPACITY = 1u, ST_NOT_CONVERGED = 2u, ST_TIMEOUT = 4u };
+
+// Device-side status and counters.  The first block of fields is cleared by
+// the host before every launch.
+struct DevStats {
+  unsigned status;
+  unsigned bar_count;
+  unsigned bar_gen;
+  unsigned flags[3];
+  unsigned windows_done;
+  unsigned pad0;
+  // persistent across launches
+  unsigned cidx;          // which copy of the double-buffered state is committed
+  unsigned max_f;
+  unsigned last_iters;
+  unsigned max_iters_seen;
+  unsigned max_win_events;      // most events one region committed in one window
+  unsigned pad1;
+  unsigned long long committed, generated, breaks, windows, iterations;
+};
+
+constexpr int kWinRing = 4096;
+
+struct KParams {
+  int L, W, H, NX, NY, NR;
+  int spans_x, spans_y;
+  unsigned long long P[10];
+  double scale;                 // 2^-F
+  uint32_t key0, key1;
+  uint32_t* rows;               // [2][H][NR]   spin rows, bit x = site x of the row
+  uint32_t* halo;               // [4][NR]      N, S, W, E halo words at t_c
+  unsigned long long* ci;       // [2][NR]      index of the pending event
+  double* cx;                   // [2][NR]      -log U of the pending event
+  unsigned long long* ckv;      // [2][NR]      V bits of the pending event
+  double* cb;                   // [2][NR]      integral of Lambda since the last event
+  double* ct;                   // [2][NR]      time up to which cb is taken
+  double* cim;                  // [2][NR]      integral over time of the region's spin sum
+  double* cib;                  // [2][NR]      integral over time of the region's owned bonds
+  double* ht;                   // [2][4][cap][NR] boundary history: times
+  uint8_t* hp;                  // [2][4][cap][NR] boundary history: positions along the edge
+  uint32_t* hl;                 // [2][4][NR]   boundary history lengths
+  int cap;
+  double* trt;                  // [NR][tcap]   committed event times (optional)
+  uint32_t* trs;                // [NR][tcap]   committed event sites
+  int tcap;
+  double* rx;                   // [K][NR]      presimulated -log U of event i at slot i mod K
+  unsigned long long* rkv;      // [K][NR]      presimulated V bits
+  unsigned long long* rhi;      // [NR]         ring holds events [committed index, rhi)
+  int K;                        // ring length (power of two)
+  int rl;                       // region lanes per block (the other threads only help fill)
+  DevStats* st;
+  uint32_t* win_iters;          // [kWinRing]
+  double t0, Tw;
+  int nwin, max_iters;
+  long long timeout_cycles;
+  int skip_block;
+};
+
+// ---------------------------------------------------------------- barrier
+// Grid-wide "synchronize" with a bounded wait (SR_TIMEOUT instead of a hang).
+__device__ __noinline__ bool grid_barrier(DevStats* st, long long timeout) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* gen = &st->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      const long long start = clock64();
+      while (*gen == g) {
+        if (clock64() - start > timeout) {
+          ok = 0;
+          atomicOr(&st->status, ST_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (*(volatile unsigned*)&st->status & ST_TIMEOUT) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------- region view
+// A lane's region: rows in shared memory (stride = threads per block), halos
+// in registers.  Bit x of row y is the spin (1 = up) of site (x, y).
+struct Region {
+  uint32_t* rows;   // rows[y * stride]
+  uint32_t* N;      // N[k * stride]
+  int stride;
+  int W, H;
+  bool spans_x, spans_y;   // the region covers the whole periodic extent
+  uint32_t wmask;
+  uint32_t hN, hS, hW, hE;
+
+  __device__ __forceinline__ uint32_t row(int y) const { return rows[y * stride]; }
+
+  // Neighbour words of row y: bit x = spin of the up/down/left/right neighbour.
+  __device__ __forceinline__ void nbr_words(int y, uint32_t r, uint32_t& up, uint32_t& dn,
+                                            uint32_t& lf, uint32_t& rt) const {
+    up = (y > 0) ? row(y - 1) : (spans_y ? row(H - 1) : hN);
+    dn = (y < H - 1) ? row(y + 1) : (spans_y ? row(0) : hS);
+    const uint32_t lbit = spans_x ? (r >> (W - 1)) & 1u : (hW >> y) & 1u;
+    const uint32_t rbit = spans_x ? (r & 1u) : (hE >> y) & 1u;
+    lf = ((r << 1) | lbit) & wmask;
+    rt = (r >> 1) | (rbit << (W - 1));
+  }
+
+  __device__ __forceinline__ int class_at(int x, int y) const {
+    const uint32_t r = row(y);
+    const int s = (r >> x) & 1;
+    const int up = (y > 0) ? (row(y - 1) >> x) & 1
+                           : (spans_y ? (row(H - 1) >> x) & 1 : (hN >> x) & 1);
+    const int dn = (y < H - 1) ? (row(y + 1) >> x) & 1 : (spans_y ? (row(0) >> x) & 1 : (hS >> x) & 1);
+    const int lf = (x > 0) ? (r >> (x - 1)) & 1 : (spans_x ? (r >> (W - 1)) & 1 : (hW >> y) & 1);
+    const int rt = (x < W - 1) ? (r >> (x + 1)) & 1 : (spans_x ? r & 1 : (hE >> y) & 1);
+    return 5 * s + up + dn + lf + rt;
+  }
+};
+
+// Per-position sum of four bits as a 3-bit number (b0, b1, b2).
+__device__ __forceinline__ void add4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t& s0,
+                                     uint32_t& s1, uint32_t& s2) {
+  const uint32_t x0 = a ^ b, c0 = a & b;
+  const uint32_t x1 = c ^ d, c1 = c & d;
+  s0 = x0 ^ x1;
+  const uint32_t c2 = x0 & x1;
+  s1 = c0 ^ c1 ^ c2;
+  s2 = (c0 & c1) | (c0 & c2) | (c1 & c2);
+}
+
+// Position of the j-th (0-based) set bit of m, j < popc(m): binary search on
+// the population counts of the low halves.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, unsigned j) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const uint32_t low = m & ((1u << w) - 1u);
+    const unsigned c = __popc(low);
+    if (j >= c) {
+      j -= c;
+      m >>= w;
+      pos += w;
+    } else {
+      m = low;
+    }
+  }
+  return pos;
+}
+
+__device__ __forceinline__ uint32_t eq_count(uint32_t s0, uint32_t s1, uint32_t s2, int n) {
+  return ((n & 1) ? s0 : ~s0) & ((n & 2) ? s1 : ~s1) & ((n & 4) ? s2 : ~s2);
+}
+
+// Class change of one site: N_k and Lambda follow (§3: "each spin flip changes
+// the class membership of several atoms").
+__device__ __forceinline__ void move_class(const Region& g, const KParams& p, int from, int to,
+                                           unsigned long long& lam) {
+  g.N[from * g.stride] -= 1u;
+  g.N[to * g.stride] += 1u;
+  lam = lam - p.P[from] + p.P[to];
+}
+
+// ---------------------------------------------------------------- region pass
+struct Acc {
+  unsigned long long events, breaks;
+  unsigned fmax, emax;
+  bool changed, overflow;
+};
+
+// One iteration of one region over [t_s, t_end): statement (a) of the §4
+// procedure, specialised in §5.  Starts from the committed state (copy cidx),
+// merges the neighbours' previous-iteration boundary lists as break points,
+// writes the tentative end state to copy cidx ^ 1 and its own boundary lists to
+// parity wp, comparing them with its lists of the previous iteration.
+__device__ void run_region(const KParams& p, int r, int wp, unsigned cidx, double t_s, double t_end,
+                           Region& g, Acc& acc) {
+  const int W = p.W, H = p.H, NR = p.NR;
+  const int rp = wp ^ 1;
+  const int rx = r % p.NX, ry = r / p.NX;
+  const size_t nr = (size_t)NR;
+
+  // ---- committed state
+  const uint32_t* rows_c = p.rows + (size_t)cidx * H * nr;
+  for (int y = 0; y < H; ++y) g.rows[y * g.stride] = rows_c[(size_t)y * nr + r];
+  g.hN = p.halo[0 * nr + r];
+  g.hS = p.halo[1 * nr + r];
+  g.hW = p.halo[2 * nr + r];
+  g.hE = p.halo[3 * nr + r];
+  unsigned long long i = p.ci[cidx * nr + r];
+  double x = p.cx[cidx * nr + r];
+  unsigned long long kv = p.ckv[cidx * nr + r];
+  double b = p.cb[cidx * nr + r];
+  double tl = p.ct[cidx * nr + r];
+  // presimulated pairs (U, V) of the coming events (§4: the random numbers
+  // as a list drawn before use); the pair of event i+1 is loaded one event ahead
+  const unsigned long long hi = p.rhi[r];
+  const unsigned long long kmask = (unsigned long long)p.K - 1ull;
+  double px = 0.0;
+  unsigned long long pkv = 0ull;
+  bool pvalid = (i + 1ull) < hi;
+  if (pvalid) {
+    const size_t a = (size_t)((i + 1ull) & kmask) * nr + r;
+    px = p.rx[a];
+    pkv = p.rkv[a];
+  }
+
+  // ---- class counts N_k, Lambda, and the region's spin / owned-bond sums
+  unsigned Nk[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) Nk[k] = 0;
+  int mag0 = 0, bond0 = 0;
+  for (int y = 0; y < H; ++y) {
+    const uint32_t rw = g.row(y);
+    uint32_t up, dn, lf, rt, s0, s1, s2;
+    g.nbr_words(y, rw, up, dn, lf, rt);
+    add4(up, dn, lf, rt, s0, s1, s2);
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+      const uint32_t e = eq_count(s0, s1, s2, n) & g.wmask;
+      Nk[5 + n] += __popc(e & rw);
+      Nk[n] += __popc(e & ~rw);
+    }
+    mag0 += 2 * __popc(rw) - W;
+    bond0 += (W - 2 * __popc((rw ^ rt) & g.wmask)) + (W - 2 * __popc((rw ^ dn) & g.wmask));
+  }
+  unsigned long long lam = 0;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    g.N[k * g.stride] = Nk[k];
+    lam += (unsigned long long)Nk[k] * p.P[k];
+  }
+
+  // ---- incoming boundary lists: the neighbours' lists of the previous iteration
+  // d = 0 N, 1 S, 2 W, 3 E; my N halo is fed by the N neighbour's S list, etc.
+  const int qN = ((ry + p.NY - 1) % p.NY) * p.NX + rx;
+  const int qS = ((ry + 1) % p.NY) * p.NX + rx;
+  const int qW = ry * p.NX + (rx + p.NX - 1) % p.NX;
+  const int qE = ry * p.NX + (rx + 1) % p.NX;
+  const double INF = __longlong_as_double(0x7FF0000000000000ll);
+  const size_t cap = (size_t)p.cap;
+  int q[4] = {qN, qS, qW, qE};
+  const int ein[4] = {1, 0, 3, 2};
+  bool has[4] = {!g.spans_y, !g.spans_y, !g.spans_x, !g.spans_x};
+  unsigned len[4], idx[4];
+  double nt[4];
+  unsigned npos[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    len[d] = has[d] ? __ldcg(&p.hl[((size_t)rp * 4 + ein[d]) * nr + q[d]]) : 0u;
+    idx[d] = 0;
+    if (len[d] > 0) {
+      const size_t a = (((size_t)rp * 4 + ein[d]) * cap) * nr + q[d];
+      nt[d] = __ldcg(&p.ht[a]);
+      npos[d] = __ldcg(&p.hp[a]);
+    } else {
+      nt[d] = INF;
+      npos[d] = 0;
+    }
+  }
+  // own lists: previous lengths for the comparison (§4, statement (c))
+  unsigned plen[4], olen[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    plen[e] = has[e] ? __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]) : 0u;
+    olen[e] = 0;
+  }
+
+  bool changed = false, overflow = false;
+  unsigned long long events = 0, brk = 0;
+  unsigned bevents = 0;
+  int ksig = 0, kbeta = 0;
+  double ssig = 0.0, sbeta = 0.0;
+  const uint32_t gx0 = (uint32_t)(rx * W), gy0 = (uint32_t)(ry * H);
+
+  double tau = tau_hat(tl, x, b, lam, p.scale);
+  for (;;) {
+    // earliest pending break point (ties: any order, a zero-length segment adds +0)
+    double tb = nt[0];
+    int db = 0;
+#pragma unroll
+    for (int d = 1; d < 4; ++d)
+      if (nt[d] < tb) { tb = nt[d]; db = d; }
+
+    if (tau <= tb) {
+      // ---- own event at tau, unless it falls past the window (§5: tau_m < t_c + T_max)
+      if (!(tau < t_end)) break;
+      // class k* of Eqs. 3.5-3.6, exactly: P = V*Lambda*2^(53+F) as a 128-bit
+      // integer (q53, rem); class k is chosen when P <= A(k) * 2^53.
+      const unsigned long long mV = 2ull * kv + 1ull;
+      const unsigned long long plo = mV * lam, phi = __umul64hi(mV, lam);
+      const unsigned long long q53 = (phi << 11) | (plo >> 53);
+      const bool exact = (plo & ((1ull << 53) - 1ull)) == 0ull;
+      unsigned long long A = 0, Aprev = 0;
+      int ks = 9;
+      for (int k = 0; k < 10; ++k) {
+        Aprev = A;
+        A += (unsigned long long)g.N[k * g.stride] * p.P[k];
+        if (q53 < A || (q53 == A && exact)) { ks = k; break; }
+      }
+      // position within the class, Eqs. 3.7-3.8: floor((V*Lambda - A(k*-1)) / p_k*)
+      const unsigned Nks = g.N[ks * g.stride];
+      unsigned long long j = (q53 - Aprev) / p.P[ks];
+      if (j >= Nks) j = Nks - 1;
+      unsigned jj = (unsigned)j;
+      // the jj-th class-k* site in row-major order (linear order of §3, Phase 3)
+      const int sp = ks >= 5;
+      const int nn = ks - 5 * sp;
+      int fx = 0, fy = 0;
+      for (int y = 0; y < H; ++y) {
+        const uint32_t rw = g.row(y);
+        uint32_t up, dn, lf, rt, s0, s1, s2;
+        g.nbr_words(y, rw, up, dn, lf, rt);
+        add4(up, dn, lf, rt, s0, s1, s2);
+        const uint32_t m = eq_count(s0, s1, s2, nn) & (sp ? rw : ~rw) & g.wmask;
+        const unsigned c = __popc(m);
+        if (jj < c) {
+          fx = nth_set_bit(m, jj);
+          fy = y;
+          break;
+        }
+        jj -= c;
+      }
+      // ---- flip (fx, fy); classes of the site and its in-region neighbours
+      const int cv = g.class_at(fx, fy);
+      const int s_old = cv >= 5;
+      const int nup = cv - 5 * s_old;
+      const int dnb = s_old ? -1 : 1;          // change of the neighbours' up count
+      int nbx[4], nby[4], nbc[4], nnb = 0;
+      if (fx < W - 1 || g.spans_x) { nbx[nnb] = (fx + 1 == W) ? 0 : fx + 1; nby[nnb] = fy; ++nnb; }
+      if (fx > 0 || g.spans_x) { nbx[nnb] = (fx == 0) ? W - 1 : fx - 1; nby[nnb] = fy; ++nnb; }
+      if (fy < H - 1 || g.spans_y) { nbx[nnb] = fx; nby[nnb] = (fy + 1 == H) ? 0 : fy + 1; ++nnb; }
+      if (fy > 0 || g.spans_y) { nbx[nnb] = fx; nby[nnb] = (fy == 0) ? H - 1 : fy - 1; ++nnb; }
+      for (int a = 0; a < nnb; ++a) nbc[a] = g.class_at(nbx[a], nby[a]);
+      g.rows[fy * g.stride] ^= (1u << fx);
+      move_class(g, p, cv, cv + (s_old ? -5 : 5), lam);
+      for (int a = 0; a < nnb; ++a) move_class(g, p, nbc[a], nbc[a] + dnb, lam);
+
+      // observables: dM = 2 sig, dBonds = 4 beta (Eq. 2.1 book-keeping)
+      const int sig = s_old ? -1 : 1;
+      const int beta = sig * (nup - 2);
+      ksig += sig;
+      ssig = (sig > 0) ? __dadd_rn(ssig, tau) : __dsub_rn(ssig, tau);
+      if (beta != 0) {
+        kbeta += beta;
+        const double bt = (beta == 2 || beta == -2) ? __dadd_rn(tau, tau) : tau;
+        sbeta = (beta > 0) ? __dadd_rn(sbeta, bt) : __dsub_rn(sbeta, bt);
+      }
+
+      // ---- boundary history (§5: the single layer of border atoms)
+      bool boundary = false;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        bool on;
+        unsigned pos;
+        if (e == 0) { on = !g.spans_y && fy == 0; pos = fx; }
+        else if (e == 1) { on = !g.spans_y && fy == H - 1; pos = fx; }
+        else if (e == 2) { on = !g.spans_x && fx == 0; pos = fy; }
+        else { on = !g.spans_x && fx == W - 1; pos = fy; }
+        if (on) {
+          boundary = true;
+          const unsigned n = olen[e];
+          if (n >= (unsigned)p.cap) {
+            overflow = true;
+          } else {
+            const size_t a = (((size_t)wp * 4 + e) * cap + n) * nr + r;
+            p.ht[a] = tau;
+            p.hp[a] = (uint8_t)pos;
+            if (n < plen[e]) {
+              const size_t pa = (((size_t)rp * 4 + e) * cap + n) * nr + r;
+              if (__double_as_longlong(__ldcg(&p.ht[pa])) != __double_as_longlong(tau) ||
+                  __ldcg(&p.hp[pa]) != (uint8_t)pos)
+                changed = true;
+            } else {
+              changed = true;
+            }
+            olen[e] = n + 1;
+          }
+        }
+      }
+      if (boundary) ++bevents;
+      if (p.tcap > 0 && i < (unsigned long long)p.tcap) {
+        p.trt[(size_t)r * p.tcap + i] = tau;
+        p.trs[(size_t)r * p.tcap + i] = (gy0 + fy) * (uint32_t)p.L + gx0 + fx;
+      }
+      ++events;
+      if (overflow) break;
+      // ---- next event: clock restarts at tau with U_{i+1} (§5, "Subsequent iterations")
+      tl = tau;
+      b = 0.0;
+      ++i;
+      if (pvalid) {
+        x = px;
+        kv = pkv;
+      } else {
+        draw_event(i, (uint32_t)r, p.key0, p.key1, x, kv);
+      }
+      pvalid = (i + 1ull) < hi;
+      if (pvalid) {
+        const size_t a = (size_t)((i + 1ull) & kmask) * nr + r;
+        px = p.rx[a];
+        pkv = p.rkv[a];
+      }
+    } else {
+      // ---- break point: a neighbour flip at tb < tau (§5, Eqs. 5.2-5.6)
+      b = accrue(b, tb, tl, lam, p.scale);
+      tl = tb;
+      const unsigned pos = npos[db];
+      int ux, uy, up_now;
+      if (db == 0) { g.hN ^= 1u << pos; up_now = (g.hN >> pos) & 1; ux = pos; uy = 0; }
+      else if (db == 1) { g.hS ^= 1u << pos; up_now = (g.hS >> pos) & 1; ux = pos; uy = H - 1; }
+      else if (db == 2) { g.hW ^= 1u << pos; up_now = (g.hW >> pos) & 1; ux = 0; uy = pos; }
+      else { g.hE ^= 1u << pos; up_now = (g.hE >> pos) & 1; ux = W - 1; uy = pos; }
+      // class of the adjacent site after the change; before it, its up count
+      // differed by one
+      const int cu_new = g.class_at(ux, uy);
+      move_class(g, p, cu_new + (up_now ? -1 : 1), cu_new, lam);
+      // advance the cursor of direction db
+      const unsigned nidx = idx[db] + 1;
+      idx[db] = nidx;
+      if (nidx < len[db]) {
+        const size_t a = (((size_t)rp * 4 + ein[db]) * cap + nidx) * nr + q[db];
+        nt[db] = __ldcg(&p.ht[a]);
+        npos[db] = __ldcg(&p.hp[a]);
+      } else {
+        nt[db] = INF;
+      }
+      ++brk;
+    }
+    tau = tau_hat(tl, x, b, lam, p.scale);
+  }
+
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (has[e]) {
+      if (olen[e] != plen[e]) changed = true;
+      p.hl[((size_t)wp * 4 + e) * nr + r] = olen[e];
+    }
+  }
+  // ---- tentative end state
+  const unsigned tc = cidx ^ 1u;
+  uint32_t* rows_t = p.rows + (size_t)tc * H * nr;
+  for (int y = 0; y < H; ++y) rows_t[(size_t)y * nr + r] = g.row(y);
+  p.ci[tc * nr + r] = i;
+  p.cx[tc * nr + r] = x;
+  p.ckv[tc * nr + r] = kv;
+  p.cb[tc * nr + r] = b;
+  p.ct[tc * nr + r] = tl;
+  const double span = __dsub_rn(t_end, t_s);
+  const double im = __dadd_rn(__dmul_rn((double)mag0, span),
+                              __dmul_rn(2.0, __dsub_rn(__dmul_rn(t_end, (double)ksig), ssig)));
+  const double ib = __dadd_rn(__dmul_rn((double)bond0, span),
+                              __dmul_rn(4.0, __dsub_rn(__dmul_rn(t_end, (double)kbeta), sbeta)));
+  p.cim[tc * nr + r] = __dadd_rn(p.cim[cidx * nr + r], im);
+  p.cib[tc * nr + r] = __dadd_rn(p.cib[cidx * nr + r], ib);
+
+  acc.events += events;
+  acc.breaks += brk;
+  if ((unsigned)events > acc.emax) acc.emax = (unsigned)events;
+  if (bevents > acc.fmax) acc.fmax = bevents;
+  acc.changed |= changed || overflow;
+  acc.overflow |= overflow;
+}
+
+// Halo words of region r from the committed rows of its four neighbours.
+__device__ void compute_halo(const KParams& p, int r, unsigned cidx) {
+  const size_t nr = (size_t)p.NR;
+  const int rx = r % p.NX, ry = r / p.NX;
+  const uint32_t* rows_c = p.rows + (size_t)cidx * p.H * nr;
+  uint32_t hN = 0, hS = 0, hW = 0, hE = 0;
+  if (!p.spans_y) {
+    const int qN = ((ry + p.NY - 1) % p.NY) * p.NX + rx;
+    const int qS = ((ry + 1) % p.NY) * p.NX + rx;
+    hN = __ldcg(&rows_c[(size_t)(p.H - 1) * nr + qN]);
+    hS = __ldcg(&rows_c[qS]);
+  }
+  if (!p.spans_x) {
+    const int qW = ry * p.NX + (rx + p.NX - 1) % p.NX;
+    const int qE = ry * p.NX + (rx + 1) % p.NX;
+    for (int y = 0; y < p.H; ++y) {
+      hW |= ((__ldcg(&rows_c[(size_t)y * nr + qW]) >> (p.W - 1)) & 1u) << y;
+      hE |= (__ldcg(&rows_c[(size_t)y * nr + qE]) & 1u) << y;
+    }
+  }
+  p.halo[0 * nr + r] = hN;
+  p.halo[1 * nr + r] = hS;
+  p.halo[2 * nr + r] = hW;
+  p.halo[3 * nr + r] = hE;
+}
+
+// ---------------------------------------------------------------- persistent kernel
+// The DO(step) / DO(iteration) loops of the §4 procedure for nwin windows.
+// Ring top-up at a window start: the block's threads together draw the pairs of
+// events [max(rhi, i_c), i_c + K) for each region of the block.
+__device__ void fill_ring(const KParams& p, unsigned cidx) {
+  const size_t nr = (size_t)p.NR;
+  const unsigned long long kmask = (unsigned long long)p.K - 1ull;
+  const int lstride = gridDim.x * p.rl;
+  for (int l = 0; l < p.rl; ++l) {
+    for (int r = blockIdx.x * p.rl + l; r < p.NR; r += lstride) {
+      const unsigned long long lo = p.ci[cidx * nr + r];
+      const unsigned long long hi_old = p.rhi[r];
+      const unsigned long long from = hi_old > lo ? hi_old : lo;
+      const unsigned long long to = lo + (unsigned long long)p.K;
+      for (unsigned long long i = from + threadIdx.x; i < to; i += blockDim.x) {
+        double x;
+        unsigned long long kv;
+        draw_event(i, (uint32_t)r, p.key0, p.key1, x, kv);
+        const size_t a = (size_t)(i & kmask) * nr + r;
+        p.rx[a] = x;
+        p.rkv[a] = kv;
+      }
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < p.rl)
+    for (int r = blockIdx.x * p.rl + threadIdx.x; r < p.NR; r += lstride)
+      p.rhi[r] = p.ci[cidx * nr + r] + (unsigned long long)p.K;
+}
+
+__global__ void __launch_bounds__(256) relax_kernel(KParams p) {
+  extern __shared__ uint32_t smem[];
+  if ((int)blockIdx.x == p.skip_block) return;   // test hook: never reaches a barrier
+  // region lanes are the first rl threads of a block; lane j of block b owns
+  // regions b*rl + j + k*(gridDim.x*rl)
+  const int stride = p.rl;
+  const bool is_lane = (int)threadIdx.x < p.rl;
+  const int gthreads = gridDim.x * p.rl;
+  const int gtid = is_lane ? (int)(blockIdx.x * p.rl + threadIdx.x) : p.NR;
+  Region g;
+  g.rows = smem + (is_lane ? threadIdx.x : 0);
+  g.N = smem + p.H * stride + (is_lane ? threadIdx.x : 0);
+  g.stride = stride;
+  g.W = p.W;
+  g.H = p.H;
+  g.spans_x = p.spans_x != 0;
+  g.spans_y = p.spans_y != 0;
+  g.wmask = (p.W == 32) ? 0xFFFFFFFFu : ((1u << p.W) - 1u);
+  DevStats* st = p.st;
+  const size_t nr = (size_t)p.NR;
+  unsigned cidx = *(volatile unsigned*)&st->cidx;
+  unsigned giter = 0;
+  double t_s = p.t0;
+
+  for (int w = 0; w < p.nwin; ++w) {
+    const double t_end = __dadd_rn(t_s, p.Tw);
+    // canonical assumption (§5): no neighbour flips -> empty previous lists
+    for (int r = gtid; r < p.NR; r += gthreads)
+      for (int e = 0; e < 4; ++e) p.hl[(size_t)e * nr + r] = 0u;   // parity 0
+    fill_ring(p, cidx);
+    if (!grid_barrier(st, p.timeout_cycles)) return;
+
+    int n = 1;
+    bool converged = false;
+    for (; n <= p.max_iters; ++n) {
+      const unsigned slot = giter % 3u;
+      ++giter;
+      const int wp = n & 1;
+      Acc acc = {0ull, 0ull, 0u, 0u, false, false};
+      for (int r = gtid; r < p.NR; r += gthreads) run_region(p, r, wp, cidx, t_s, t_end, g, acc);
+      if (acc.changed) atomicOr(&st->flags[slot], 1u);
+      if (acc.overflow) atomicOr(&st->status, ST_CAPACITY);
+      if (acc.events) atomicAdd(&st->generated, acc.events);
+      if (acc.breaks) atomicAdd(&st->breaks, acc.breaks);
+      if (acc.fmax) atomicMax(&st->max_f, acc.fmax);
+      if (acc.emax) atomicMax(&st->max_win_events, acc.emax);
+      if (!grid_barrier(st, p.timeout_cycles)) return;
+      if (blockIdx.x == 0 && threadIdx.x == 0) st->flags[(slot + 2u) % 3u] = 0u;
+      if (*(volatile unsigned*)&st->status & ST_CAPACITY) return;   // window not committed
+      if (*(volatile unsigned*)&st->flags[slot] == 0u) {
+        converged = true;
+        break;
+      }
+    }
+    if (!converged) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&st->status, ST_NOT_CONVERGED);
+      return;
+    }
+    // ---- commit (statement 3 of §4: increment committed time by T_max)
+    unsigned long long committed = 0;
+    for (int r = gtid; r < p.NR; r += gthreads)
+      committed += p.ci[(cidx ^ 1u) * nr + r] - p.ci[cidx * nr + r];
+    if (committed) atomicAdd(&st->committed, committed);
+    cidx ^= 1u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->cidx = cidx;
+      st->windows += 1ull;
+      st->iterations += (unsigned long long)n;
+      st->last_iters = (unsigned)n;
+      if ((unsigned)n > st->max_iters_seen) st->max_iters_seen = (unsigned)n;
+      p.win_iters[w % kWinRing] = (unsigned)n;
+      st->windows_done = (unsigned)(w + 1);
+    }
+    if (!grid_barrier(st, p.timeout_cycles)) return;
+    for (int r = gtid; r < p.NR; r += gthreads) compute_halo(p, r, cidx);
+    if (!grid_barrier(st, p.timeout_cycles)) return;
+    t_s = t_end;
+  }
+}
+
+// ---------------------------------------------------------------- helpers
+__global__ void halo_kernel(KParams p, unsigned cidx) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < p.NR) compute_halo(p, r, cidx);
+}
+
+// Fair coin / all up / all down rows (copy 0).
+__global__ void init_rows_kernel(KParams p, int mode) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)p.NR * p.H) return;
+  const int r = (int)(t % p.NR), y = (int)(t / p.NR);
+  const int rx = r % p.NX, ry = r / p.NX;
+  uint32_t word = 0;
+  if (mode == SR_INIT_ALL_UP) {
+    word = (p.W == 32) ? 0xFFFFFFFFu : ((1u << p.W) - 1u);
+  } else if (mode == SR_INIT_FAIR_COIN) {
+    const uint32_t gy = (uint32_t)(ry * p.H + y);
+    for (int x = 0; x < p.W; ++x) {
+      const uint32_t site = gy * (uint32_t)p.L + (uint32_t)(rx * p.W + x);
+      uint32_t w[4];
+      philox4x32_10(site, 0u, 0u, 1u, p.key0, p.key1, w);
+      word |= (w[0] & 1u) << x;
+    }
+  }
+  p.rows[(size_t)y * p.NR + r] = word;
+}
+
+// Rows (copy 0) from an int8 lattice in device memory.
+__global__ void pack_rows_kernel(KParams p, const int8_t* spins) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)p.NR * p.H) return;
+  const int r = (int)(t % p.NR), y = (int)(t / p.NR);
+  const int rx = r % p.NX, ry = r / p.NX;
+  const size_t base = (size_t)(ry * p.H + y) * p.L + (size_t)rx * p.W;
+  uint32_t word = 0;
+  for (int x = 0; x < p.W; ++x) word |= (uint32_t)(spins[base + x] > 0) << x;
+  p.rows[(size_t)y * p.NR + r] = word;
+}
+
+__global__ void unpack_rows_kernel(KParams p, unsigned cidx, int8_t* spins) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)p.L * p.L) return;
+  const int gx = (int)(t % p.L), gy = (int)(t / p.L);
+  const int r = (gy / p.H) * p.NX + gx / p.W;
+  const uint32_t word = p.rows[((size_t)cidx * p.H + gy % p.H) * p.NR + r];
+  spins[t] = ((word >> (gx % p.W)) & 1u) ? 1 : -1;
+}
+
+// Clock state at t = 0: tau_0 = 0, first pair (U_1, V_1) of every region.
+__global__ void init_carry_kernel(KParams p) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= p.NR) return;
+  double x;
+  unsigned long long kv;
+  draw_event(0ull, (uint32_t)r, p.key0, p.key1, x, kv);
+  p.ci[r] = 0ull;
+  p.cx[r] = x;
+  p.ckv[r] = kv;
+  p.cb[r] = 0.0;
+  p.ct[r] = 0.0;
+  p.cim[r] = 0.0;
+  p.cib[r] = 0.0;
+  p.rhi[r] = 0ull;   // ring empty
+}
+
+// Spin sum and owned-bond sum (right and down bonds of every site), exact.
+__global__ void observe_ints_kernel(KParams p, unsigned cidx, long long* out2) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  long long mag = 0, bonds = 0;
+  if (r < p.NR) {
+    const size_t nr = (size_t)p.NR;
+    const uint32_t wmask = (p.W == 32) ? 0xFFFFFFFFu : ((1u << p.W) - 1u);
+    const uint32_t* rows_c = p.rows + (size_t)cidx * p.H * nr;
+    const uint32_t hS = p.halo[1 * nr + r], hE = p.halo[3 * nr + r];
+    for (int y = 0; y < p.H; ++y) {
+      const uint32_t rw = rows_c[(size_t)y * nr + r];
+      const uint32_t dn = (y < p.H - 1) ? rows_c[(size_t)(y + 1) * nr + r]
+                                        : (p.spans_y ? rows_c[r] : hS);
+      const uint32_t rbit = p.spans_x ? (rw & 1u) : (hE >> y) & 1u;
+      const uint32_t rt = (rw >> 1) | (rbit << (p.W - 1));
+      mag += 2 * __popc(rw) - p.W;
+      bonds += (p.W - 2 * __popc((rw ^ rt) & wmask)) + (p.W - 2 * __popc((rw ^ dn) & wmask));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mag += __shfl_down_sync(0xFFFFFFFFu, mag, o);
+    bonds += __shfl_down_sync(0xFFFFFFFFu, bonds, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd((unsigned long long*)&out2[0], (unsigned long long)mag);
+    atomicAdd((unsigned long long*)&out2[1], (unsigned long long)bonds);
+  }
+}
+
+// Fixed-order FP64 sums of the per-region time integrals (one block).
+__global__ void observe_integrals_kernel(KParams p, unsigned cidx, double* out2) {
+  __shared__ double sm[2][1024];
+  const size_t nr = (size_t)p.NR;
+  double a = 0.0, c = 0.0;
+  for (size_t r = threadIdx.x; r < nr; r += blockDim.x) {
+    a = __dadd_rn(a, p.cim[cidx * nr + r]);
+    c = __dadd_rn(c, p.cib[cidx * nr + r]);
+  }
+  sm[0][threadIdx.x] = a;
+  sm[1][threadIdx.x] = c;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sm[0][threadIdx.x] = __dadd_rn(sm[0][threadIdx.x], sm[0][threadIdx.x + s]);
+      sm[1][threadIdx.x] = __dadd_rn(sm[1][threadIdx.x], sm[1][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out2[0] = sm[0][0];
+    out2[1] = sm[1][0];
+  }
+}
+
+__global__ void eval_draws_kernel(uint32_t key0, uint32_t key1, uint32_t region,
+                                  unsigned long long i0, size_t n, double* x,
+                                  unsigned long long* kv) {
+  const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double xx;
+  unsigned long long k;
+  draw_event(i0 + j, region, key0, key1, xx, k);
+  x[j] = xx;
+  kv[j] = k;
+}
+
+}  // namespace sr
+
+// ====================================================================== C ABI
+using namespace sr;
+
+struct sr_ctx {
+  sr_params prm;
+  int NX, NY, NR, F;
+  unsigned long long P[10];
+  double scale;
+  cudaStream_t stream;
+  bool own_stream;
+  int num_sms;
+  int clock_khz;
+  uint32_t *rows, *halo, *hl, *trs, *win_iters;
+  unsigned long long *ci, *ckv, *rkv, *rhi;
+  double* rx;
+  int K, Kcap;
+  double *cx, *cb, *ct, *cim, *cib, *ht, *trt;
+  uint8_t* hp;
+  int cap;
+  bool cap_auto;
+  DevStats* st;
+  DevStats* h_st;
+  long long* obs_i;
+  double* obs_f;
+  long long* h_obs_i;
+  double* h_obs_f;
+  int8_t* stage;
+  double t_c;
+  int rl, tpb, blocks;
+  size_t smem;
+  int last_nwin;
+  unsigned long long launches;   // kernels launched by this context
+};
+
+namespace {
+
+constexpr int kMaxCap = 1 << 16;
+
+int bitlen(long long v) {
+  int b = 0;
+  while ((v >> b) > 0) ++b;
+  return b;
+}
+
+// p_k for the ten classes k = 5*[s=+1] + n_up (Eqs. 2.2-2.3), then the
+// fixed-point grid P_k = round(p_k 2^F), F = 63 - bitlen(sites per region).
+void rate_table(const sr_params& p, int F, unsigned long long P[10]) {
+  for (int k = 0; k < 10; ++k) {
+    const int s = (k >= 5) ? 1 : -1;
+    const int n_up = k % 5;
+    const int nb_sum = 2 * n_up - 4;
+    const double dE = 2.0 * (double)s * (p.J * (double)nb_sum + p.h);
+    const double theta = std::exp(-dE / p.T);
+    double pk;
+    if (p.rates == SR_RATES_GLAUBER)
+      pk = theta / (1.0 + theta);
+    else
+      pk = theta < 1.0 ? theta : 1.0;
+    P[k] = (unsigned long long)std::nearbyint(std::ldexp(pk, F));
+  }
+}
+
+KParams make_params(const sr_ctx* c) {
+  KParams k;
+  std::memset(&k, 0, sizeof k);
+  k.L = c->prm.L;
+  k.W = c->prm.region_w;
+  k.H = c->prm.region_h;
+  k.NX = c->NX;
+  k.NY = c->NY;
+  k.NR = c->NR;
+  k.spans_x = c->NX == 1;
+  k.spans_y = c->NY == 1;
+  for (int i = 0; i < 10; ++i) k.P[i] = c->P[i];
+  k.scale = c->scale;
+  k.key0 = (uint32_t)c->prm.seed;
+  k.key1 = (uint32_t)(c->prm.seed >> 32);
+  k.rows = c->rows;
+  k.halo = c->halo;
+  k.ci = c->ci;
+  k.cx = c->cx;
+  k.ckv = c->ckv;
+  k.cb = c->cb;
+  k.ct = c->ct;
+  k.cim = c->cim;
+  k.cib = c->cib;
+  k.ht = c->ht;
+  k.hp = c->hp;
+  k.hl = c->hl;
+  k.cap = c->cap;
+  k.trt = c->trt;
+  k.trs = c->trs;
+  k.tcap = c->prm.trace_capacity;
+  k.rx = c->rx;
+  k.rkv = c->rkv;
+  k.rhi = c->rhi;
+  k.K = c->K;
+  k.rl = c->rl;
+  k.st = c->st;
+  k.win_iters = c->win_iters;
+  k.max_iters = c->prm.max_iters;
+  k.timeout_cycles = (long long)c->prm.barrier_timeout_ms * (long long)c->clock_khz;
+  k.skip_block = c->prm.test_barrier_skip_block;
+  return k;
+}
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T)) == cudaSuccess ? SR_OK : SR_ENOMEM;
+}
+
+int alloc_history(sr_ctx* c, int cap) {
+  if (c->ht) cudaFree(c->ht);
+  if (c->hp) cudaFree(c->hp);
+  c->ht = nullptr;
+  c->hp = nullptr;
+  const size_t n = (size_t)2 * 4 * (size_t)cap * (size_t)c->NR;
+  if (dalloc(&c->ht, n) || dalloc(&c->hp, n)) return SR_ENOMEM;
+  c->cap = cap;
+  return SR_OK;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SR_OK : SR_ECUDA; }
+
+// Initial state: rows (copy 0) come from the caller or the init kernel.
+int init_state(sr_ctx* c, const int8_t* dev_spins) {
+  KParams k = make_params(c);
+  const size_t nrow = (size_t)c->NR * c->prm.region_h;
+  const unsigned gb = (unsigned)((nrow + 255) / 256);
+  if (dev_spins)
+    pack_rows_kernel<<<gb, 256, 0, c->stream>>>(k, dev_spins);
+  else
+    init_rows_kernel<<<gb, 256, 0, c->stream>>>(k, c->prm.init_mode);
+  halo_kernel<<<(c->NR + 255) / 256, 256, 0, c->stream>>>(k, 0u);
+  init_carry_kernel<<<(c->NR + 255) / 256, 256, 0, c->stream>>>(k);
+  c->launches += 3;
+  if (cudaMemsetAsync(c->st, 0, sizeof(DevStats), c->stream) != cudaSuccess) return SR_ECUDA;
+  c->t_c = 0.0;
+  c->last_nwin = 0;
+  return cuda_rc(cudaGetLastError());
+}
+
+int launch_relax(sr_ctx* c, double t0, double Tw, int nwin) {
+  KParams k = make_params(c);
+  k.t0 = t0;
+  k.Tw = Tw;
+  k.nwin = nwin;
+  if (cudaMemsetAsync(c->st, 0, offsetof(DevStats, cidx), c->stream) != cudaSuccess) return SR_ECUDA;
+  void* args[] = {&k};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)relax_kernel, dim3(c->blocks),
+                                              dim3(c->tpb), args, c->smem, c->stream);
+  if (e != cudaSuccess) return SR_ECUDA;
+  c->launches += 1;
+  if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return SR_ECUDA;
+  return cuda_rc(cudaStreamSynchronize(c->stream));
+}
+
+// Ring length for windows of length Tw: at most sites * Tw events are expected
+// per region (every p_k <= 1), with a margin; events past the ring are drawn on
+// the fly, so the cap only bounds memory.
+int ring_length(const sr_ctx* c, double Tw) {
+  const double want = 1.25 * (double)c->prm.region_w * c->prm.region_h * Tw + 16.0;
+  int K = 16;
+  while (K < want && K < 4096) K *= 2;
+  return K;
+}
+
+int set_ring(sr_ctx* c, int K) {
+  if (K == c->K) return SR_OK;
+  if (K > c->Kcap) {
+    if (c->rx) cudaFree(c->rx);
+    if (c->rkv) cudaFree(c->rkv);
+    c->rx = nullptr;
+    c->rkv = nullptr;
+    c->Kcap = 0;
+    c->K = 0;
+    const size_t n = (size_t)K * c->NR;
+    if (dalloc(&c->rx, n) || dalloc(&c->rkv, n)) return SR_ENOMEM;
+    c->Kcap = K;
+  }
+  c->K = K;
+  // slots are indexed modulo K: a new K invalidates every ring
+  return cuda_rc(cudaMemsetAsync(c->rhi, 0, (size_t)c->NR * sizeof(unsigned long long), c->stream));
+}
+
+void free_all(sr_ctx* c) {
+  void* dev[] = {c->rows, c->halo, c->hl, c->trs, c->win_iters, c->ci, c->ckv, c->cx, c->cb,
+                 c->ct, c->cim, c->cib, c->ht, c->trt, c->hp, c->st, c->obs_i, c->obs_f, c->stage,
+                 c->rx, c->rkv, c->rhi};
+  for (void* d : dev)
+    if (d) cudaFree(d);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  if (c->h_obs_i) cudaFreeHost(c->h_obs_i);
+  if (c->h_obs_f) cudaFreeHost(c->h_obs_f);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sr_strerror(int code) {
+  switch (code) {
+    case SR_OK: return "ok";
+    case SR_EINVAL: return "invalid argument";
+    case SR_ENOMEM: return "out of memory";
+    case SR_ECUDA: return "CUDA error";
+    case SR_NOT_CONVERGED: return "relaxation did not converge within the iteration cap";
+    case SR_CAPACITY: return "boundary history exceeded the largest capacity";
+    case SR_TIMEOUT: return "grid-wide synchronize timed out";
+    case SR_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+int sr_create_ex(sr_ctx** out, const sr_params* prm) {
+  if (!out || !prm) return SR_EINVAL;
+  *out = nullptr;
+  const sr_params& p = *prm;
+  if (p.L < 3 || p.region_w < 1 || p.region_h < 1 || p.L % p.region_w || p.L % p.region_h)
+    return SR_EINVAL;
+  if (!(p.T > 0.0) || !std::isfinite(p.J) || !std::isfinite(p.h) || std::isnan(p.T)) return SR_EINVAL;
+  if (p.init_mode < SR_INIT_FAIR_COIN || p.init_mode > SR_INIT_ALL_DOWN) return SR_EINVAL;
+  if (p.rates != SR_RATES_METROPOLIS && p.rates != SR_RATES_GLAUBER) return SR_EINVAL;
+  if (p.capacity < 0 || p.max_iters < 0 || p.trace_capacity < 0 || p.threads_per_block < 0 ||
+      p.block_threads < 0 || p.blocks < 0 || p.barrier_timeout_ms < 0)
+    return SR_EINVAL;
+  if (p.region_w > 32 || p.region_h > 32) return SR_EUNSUPPORTED;
+  if ((long long)p.L * p.L > (1ll << 32)) return SR_EUNSUPPORTED;
+
+  sr_ctx* c = (sr_ctx*)std::calloc(1, sizeof(sr_ctx));
+  if (!c) return SR_ENOMEM;
+  c->prm = p;
+  if (c->prm.max_iters == 0) c->prm.max_iters = 1 << 16;
+  if (c->prm.barrier_timeout_ms == 0) c->prm.barrier_timeout_ms = 2000;
+  c->NX = p.L / p.region_w;
+  c->NY = p.L / p.region_h;
+  c->NR = c->NX * c->NY;
+  c->F = 63 - bitlen((long long)p.region_w * p.region_h);
+  c->scale = std::ldexp(1.0, -c->F);
+  rate_table(c->prm, c->F, c->P);
+
+  int rc = SR_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+    std::free(c);
+    return SR_ECUDA;
+  }
+  if (p.stream) {
+    c->stream = (cudaStream_t)p.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      std::free(c);
+      return SR_ECUDA;
+    }
+    c->own_stream = true;
+  }
+
+  // launch shape: spread the regions over every SM, one lane per region; a
+  // block with few region lanes gets helper threads for the ring top-up
+  const int H = p.region_h;
+  int rl = p.threads_per_block;
+  if (rl == 0) {
+    const int per_sm = (c->NR + c->num_sms - 1) / c->num_sms;
+    const int bps = (per_sm + 255) / 256;              // blocks per SM
+    rl = (per_sm + bps - 1) / bps;
+    if (rl > 32) rl = ((rl + 31) / 32) * 32;
+    if (rl > 256) rl = 256;
+    if (rl < 1) rl = 1;
+  }
+  if (rl > 256) rl = 256;
+  int tpb = p.block_threads ? p.block_threads : ((rl + 31) / 32) * 32;
+  if (!p.block_threads && tpb < 128) tpb = 128;
+  if (tpb < rl) tpb = rl;
+  if (tpb > 256) tpb = 256;
+  c->rl = rl;
+  c->tpb = tpb;
+  c->smem = (size_t)(H + 10) * rl * sizeof(uint32_t);
+  int per_sm_blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel, tpb, c->smem) !=
+          cudaSuccess ||
+      per_sm_blocks < 1) {
+    free_all(c);
+    std::free(c);
+    return SR_EUNSUPPORTED;
+  }
+  const int want = (c->NR + rl - 1) / rl;
+  int blocks = p.blocks ? p.blocks : want;
+  const int max_res = per_sm_blocks * c->num_sms;
+  if (blocks > max_res) blocks = max_res;
+  c->blocks = blocks;
+
+  const size_t nr = (size_t)c->NR;
+  rc |= dalloc(&c->rows, 2 * (size_t)H * nr);
+  rc |= dalloc(&c->halo, 4 * nr);
+  rc |= dalloc(&c->ci, 2 * nr);
+  rc |= dalloc(&c->cx, 2 * nr);
+  rc |= dalloc(&c->ckv, 2 * nr);
+  rc |= dalloc(&c->cb, 2 * nr);
+  rc |= dalloc(&c->ct, 2 * nr);
+  rc |= dalloc(&c->cim, 2 * nr);
+  rc |= dalloc(&c->cib, 2 * nr);
+  rc |= dalloc(&c->hl, 2 * 4 * nr);
+  rc |= dalloc(&c->st, 1);
+  rc |= dalloc(&c->win_iters, kWinRing);
+  rc |= dalloc(&c->obs_i, 2);
+  rc |= dalloc(&c->obs_f, 2);
+  rc |= dalloc(&c->stage, (size_t)p.L * p.L);
+  rc |= dalloc(&c->rhi, nr);
+  if (p.trace_capacity > 0) {
+    rc |= dalloc(&c->trt, nr * (size_t)p.trace_capacity);
+    rc |= dalloc(&c->trs, nr * (size_t)p.trace_capacity);
+  }
+  c->cap_auto = p.capacity == 0;
+  if (rc == SR_OK) rc = alloc_history(c, p.capacity ? p.capacity : 64);
+  if (rc == SR_OK &&
+      (cudaMallocHost((void**)&c->h_st, sizeof(DevStats)) != cudaSuccess ||
+       cudaMallocHost((void**)&c->h_obs_i, 2 * sizeof(long long)) != cudaSuccess ||
+       cudaMallocHost((void**)&c->h_obs_f, 2 * sizeof(double)) != cudaSuccess))
+    rc = SR_ENOMEM;
+  if (rc == SR_OK && cudaMemsetAsync(c->hl, 0, 2 * 4 * nr * sizeof(uint32_t), c->stream) != cudaSuccess)
+    rc = SR_ECUDA;
+  if (rc == SR_OK) rc = init_state(c, nullptr);
+  if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
+  if (rc != SR_OK) {
+    free_all(c);
+    std::free(c);
+    return rc == SR_ENOMEM ? SR_ENOMEM : (rc < 0 ? rc : SR_ECUDA);
+  }
+  *out = c;
+  return SR_OK;
+}
+
+int sr_create(sr_ctx** out, int L, double J, double h, double T, int region_w, int region_h,
+              uint64_t seed) {
+  sr_params p;
+  std::memset(&p, 0, sizeof p);
+  p.L = L;
+  p.J = J;
+  p.h = h;
+  p.T = T;
+  p.region_w = region_w;
+  p.region_h = region_h;
+  p.seed = seed;
+  p.init_mode = SR_INIT_FAIR_COIN;
+  p.rates = SR_RATES_METROPOLIS;
+  p.test_barrier_skip_block = -1;
+  return sr_create_ex(out, &p);
+}
+
+void sr_destroy(sr_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  std::free(c);
+}
+
+int sr_run_windows(sr_ctx* c, double t0, double Tw, int n) {
+  if (!c || n < 1 || !(Tw > 0.0) || !std::isfinite(Tw)) return SR_EINVAL;
+  if (t0 != c->t_c) return SR_EINVAL;
+  double t = t0;
+  int remaining = n;
+  c->last_nwin = 0;
+  int rc0 = set_ring(c, ring_length(c, Tw));
+  if (rc0 != SR_OK) return rc0;
+  while (remaining > 0) {
+    int rc = launch_relax(c, t, Tw, remaining);
+    if (rc != SR_OK) return rc;
+    const DevStats& h = *c->h_st;
+    const int done = (int)h.windows_done;
+    for (int w = 0; w < done; ++w) t = t + Tw;
+    c->t_c = t;
+    c->last_nwin += done;
+    remaining -= done;
+    if (h.status == 0u) {
+      if (remaining != 0) return SR_ECUDA;   // kernel ended early without a reason
+      break;
+    }
+    if (h.status & ST_TIMEOUT) return SR_TIMEOUT;
+    if (h.status & ST_NOT_CONVERGED) return SR_NOT_CONVERGED;
+    if (h.status & ST_CAPACITY) {
+      if (!c->cap_auto || c->cap >= kMaxCap) return SR_CAPACITY;
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
+      rc = alloc_history(c, c->cap * 2);
+      if (rc != SR_OK) return rc;
+      continue;
+    }
+    return SR_ECUDA;
+  }
+  return SR_OK;
+}
+
+int sr_run_window(sr_ctx* c, double t0, double Tw) { return sr_run_windows(c, t0, Tw, 1); }
+
+int sr_observables(sr_ctx* c, sr_obs* out) {
+  if (!c || !out) return SR_EINVAL;
+  KParams k = make_params(c);
+  if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return SR_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
+  const unsigned cidx = c->h_st->cidx;
+  if (cudaMemsetAsync(c->obs_i, 0, 2 * sizeof(long long), c->stream) != cudaSuccess) return SR_ECUDA;
+  observe_ints_kernel<<<(c->NR + 255) / 256, 256, 0, c->stream>>>(k, cidx, c->obs_i);
+  observe_integrals_kernel<<<1, 1024, 0, c->stream>>>(k, cidx, c->obs_f);
+  if (cudaGetLastError() != cudaSuccess) return SR_ECUDA;
+  c->launches += 2;
+  cudaMemcpyAsync(c->h_obs_i, c->obs_i, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(c->h_obs_f, c->obs_f, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
+  const DevStats& h = *c->h_st;
+  std::memset(out, 0, sizeof *out);
+  out->t_c = c->t_c;
+  out->mag = c->h_obs_i[0];
+  out->bonds = c->h_obs_i[1];
+  const double sites = (double)c->prm.L * (double)c->prm.L;
+  out->m = (double)out->mag / sites;
+  out->E = -c->prm.J * (double)out->bonds - c->prm.h * (double)out->mag;
+  out->int_mag = c->h_obs_f[0];
+  out->int_bonds = c->h_obs_f[1];
+  out->committed = h.committed;
+  out->generated = h.generated;
+  out->breaks = h.breaks;
+  out->windows = h.windows;
+  out->iterations = h.iterations;
+  out->last_iters = h.last_iters;
+  out->max_iters_seen = h.max_iters_seen;
+  out->max_f = h.max_f;
+  out->capacity = (uint32_t)c->cap;
+  out->launches = c->launches;
+  return SR_OK;
+}
+
+static int committed_index(sr_ctx* c, unsigned* cidx) {
+  if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return SR_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
+  *cidx = c->h_st->cidx;
+  return SR_OK;
+}
+
+int sr_get_spins_device(sr_ctx* c, int8_t* dev_out, size_t n) {
+  if (!c || !dev_out || n != (size_t)c->prm.L * c->prm.L) return SR_EINVAL;
+  unsigned cidx;
+  int rc = committed_index(c, &cidx);
+  if (rc) return rc;
+  KParams k = make_params(c);
+  unpack_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(k, cidx, dev_out);
+  c->launches += 1;
+  return cuda_rc(cudaGetLastError());
+}
+
+int sr_get_spins(sr_ctx* c, int8_t* host_out, size_t n) {
+  if (!c || !host_out) return SR_EINVAL;
+  int rc = sr_get_spins_device(c, c->stage, n);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(host_out, c->stage, n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  return cuda_rc(cudaStreamSynchronize(c->stream));
+}
+
+int sr_set_spins_device(sr_ctx* c, const int8_t* dev_in, size_t n) {
+  if (!c || !dev_in || n != (size_t)c->prm.L * c->prm.L) return SR_EINVAL;
+  return init_state(c, dev_in);
+}
+
+int sr_set_spins(sr_ctx* c, const int8_t* host_in, size_t n) {
+  if (!c || !host_in || n != (size_t)c->prm.L * c->prm.L) return SR_EINVAL;
+  if (cudaMemcpyAsync(c->stage, host_in, n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  int rc = init_state(c, c->stage);
+  if (rc) return rc;
+  return cuda_rc(cudaStreamSynchronize(c->stream));
+}
+
+int sr_reset(sr_ctx* c) {
+  if (!c) return SR_EINVAL;
+  int rc = init_state(c, nullptr);
+  if (rc) return rc;
+  return cuda_rc(cudaStreamSynchronize(c->stream));
+}
+
+int sr_get_carry(sr_ctx* c, uint64_t* index, double* x, double* b, double* t_last, size_t n) {
+  if (!c || n != (size_t)c->NR) return SR_EINVAL;
+  unsigned cidx;
+  int rc = committed_index(c, &cidx);
+  if (rc) return rc;
+  const size_t off = (size_t)cidx * c->NR;
+  if (index) cudaMemcpyAsync(index, c->ci + off, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (x) cudaMemcpyAsync(x, c->cx + off, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (b) cudaMemcpyAsync(b, c->cb + off, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (t_last) cudaMemcpyAsync(t_last, c->ct + off, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  return cuda_rc(cudaStreamSynchronize(c->stream));
+}
+
+int sr_get_trace(sr_ctx* c, uint64_t* lens, double* times, uint32_t* sites, size_t n_regions,
+                 size_t cap) {
+  if (!c || n_regions != (size_t)c->NR) return SR_EINVAL;
+  if ((times || sites) && (c->prm.trace_capacity == 0 || cap != (size_t)c->prm.trace_capacity))
+    return SR_EINVAL;
+  unsigned cidx;
+  int rc = committed_index(c, &cidx);
+  if (rc) return rc;
+  const size_t total = n_regions * cap;
+  if (lens)
+    cudaMemcpyAsync(lens, c->ci + (size_t)cidx * c->NR, n_regions * 8, cudaMemcpyDeviceToHost,
+                    c->stream);
+  if (times) cudaMemcpyAsync(times, c->trt, total * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (sites) cudaMemcpyAsync(sites, c->trs, total * 4, cudaMemcpyDeviceToHost, c->stream);
+  return cuda_rc(cudaStreamSynchronize(c->stream));
+}
+
+int sr_get_window_iters(sr_ctx* c, uint32_t* out, size_t n) {
+  if (!c || !out) return SR_EINVAL;
+  const int have = c->last_nwin < kWinRing ? c->last_nwin : kWinRing;
+  const int m = (int)n < have ? (int)n : have;
+  if (m <= 0) return 0;
+  uint32_t* tmp = (uint32_t*)std::malloc(kWinRing * sizeof(uint32_t));
+  if (!tmp) return SR_ENOMEM;
+  if (cudaMemcpyAsync(tmp, c->win_iters, kWinRing * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    std::free(tmp);
+    return SR_ECUDA;
+  }
+  // the last launch wrote windows 0.. of its own count; a retried call
+  // (capacity growth) restarts the ring at 0, so the last m entries written
+  // are the last windows of the final launch
+  const int last_launch = (int)c->h_st->windows_done;
+  for (int i = 0; i < m; ++i) {
+    const int w = last_launch - m + i;
+    out[i] = tmp[((w % kWinRing) + kWinRing) % kWinRing];
+  }
+  std::free(tmp);
+  return m;
+}
+
+int sr_eval_draws(uint64_t seed, uint32_t region, uint64_t i0, size_t n, double* x, uint64_t* kV) {
+  if (n == 0) return SR_OK;
+  double* dx = nullptr;
+  unsigned long long* dk = nullptr;
+  if (dalloc(&dx, n) || dalloc(&dk, n)) {
+    if (dx) cudaFree(dx);
+    if (dk) cudaFree(dk);
+    return SR_ENOMEM;
+  }
+  eval_draws_kernel<<<(unsigned)((n + 255) / 256), 256>>>((uint32_t)seed, (uint32_t)(seed >> 32),
+                                                          region, i0, n, dx, dk);
+  int rc = cuda_rc(cudaGetLastError());
+  if (rc == SR_OK && x) rc = cuda_rc(cudaMemcpy(x, dx, n * 8, cudaMemcpyDeviceToHost));
+  if (rc == SR_OK && kV) rc = cuda_rc(cudaMemcpy(kV, dk, n * 8, cudaMemcpyDeviceToHost));
+  cudaFree(dx);
+  cudaFree(dk);
+  return rc;
+}
+
+int sr_get_info(sr_ctx* c, int* n_regions, int* frac_bits, uint64_t* P, int* threads_per_block,
+                int* blocks) {
+  if (!c) return SR_EINVAL;
+  if (n_regions) *n_regions = c->NR;
+  if (frac_bits) *frac_bits = c->F;
+  if (P)
+    for (int k = 0; k < 10; ++k) P[k] = c->P[k];
+  if (threads_per_block) *threads_per_block = c->rl;
+  if (blocks) *blocks = c->blocks;
+  return SR_OK;
+}
+
+}  // extern "C"
