@@ -41,6 +41,7 @@ extern "C" {
 #define SR_CAPACITY (-5)        /* boundary history larger than the largest allowed capacity */
 #define SR_TIMEOUT (-6)         /* a grid-wide synchronize waited longer than its limit */
 #define SR_EUNSUPPORTED (-7)    /* valid but not supported by this build (e.g. region wider than 32) */
+#define SR_ETOOLARGE (-8)       /* problem needs more than the fixed scratch of sr_run_noalloc */
 
 /* ---- initial spins ---- */
 #define SR_INIT_FAIR_COIN 0     /* bit 0 of Philox4x32-10(counter = (site, 0, 0, 1), key = seed) */
@@ -186,6 +187,34 @@ int sr_get_info(sr_ctx* ctx, int* n_regions, int* frac_bits, uint64_t* P, int* t
  * Host arrays of n entries; either may be NULL.  Blocks until done.  Errors:
  * SR_EINVAL, SR_ENOMEM, SR_ECUDA. */
 int sr_eval_draws(uint64_t seed, uint32_t region, uint64_t i0, size_t n, double* x, uint64_t* kV);
+
+/* Run a whole simulation without allocating any memory.  The paper has no
+ * counterpart: this exists for callers that cannot allocate GPU memory at the
+ * point where they simulate, e.g. code that runs inside a memory-pool budget
+ * that must not grow, plug-ins whose host forbids cudaMalloc/cudaFree in their
+ * callbacks, or long-running services that pre-plan every allocation.
+ *
+ * It simulates an L x L lattice from t = 0 through n_windows windows of length
+ * Tw (same method, same results as sr_create + sr_run_windows with automatic
+ * settings except a fixed history capacity) and writes the final spins.  All
+ * working state lives in one fixed scratch array of SR_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading this library holds until the process exits.
+ *   spins_in   device, L*L int8 (> 0 = up), or NULL for fair-coin spins from seed
+ *   spins_out  device, L*L int8, caller-owned, written with the spins at the end
+ *   counts_out device, (L/region_w)*(L/region_h) uint64 committed events per
+ *              region, or NULL
+ *   stream     cudaStream_t to run on, or NULL for the default stream
+ * The call blocks until done.  On the first call on a device it looks up the
+ * scratch address for that device, so make that first call before any stream
+ * capture.  Every call uses the same scratch: calls that overlap on the GPU
+ * (other threads, other streams) race and must not be made.  Errors: SR_EINVAL,
+ * SR_ETOOLARGE (the state does not fit the scratch), SR_EUNSUPPORTED,
+ * SR_CAPACITY (more than 64 boundary events on one region edge in one
+ * iteration), SR_NOT_CONVERGED, SR_TIMEOUT, SR_ECUDA. */
+#define SR_NOALLOC_SCRATCH_BYTES (8u << 20)
+int sr_run_noalloc(int L, double J, double h, double T, int region_w, int region_h, uint64_t seed,
+                   const int8_t* spins_in, double Tw, int n_windows, int8_t* spins_out,
+                   uint64_t* counts_out, void* stream);
 
 /* Name of a status code (static string). */
 const char* sr_strerror(int code);

@@ -986,6 +986,7 @@ const char* sr_strerror(int code) {
     case SR_CAPACITY: return "boundary history exceeded the largest capacity";
     case SR_TIMEOUT: return "grid-wide synchronize timed out";
     case SR_EUNSUPPORTED: return "unsupported configuration";
+    case SR_ETOOLARGE: return "problem does not fit the fixed no-allocation scratch";
     default: return "unknown status";
   }
 }
@@ -1347,3 +1348,181 @@ int sr_get_info(sr_ctx* c, int* n_regions, int* frac_bits, uint64_t* P, int* thr
 }
 
 }  // extern "C"
+
+// ====================================================================== no-allocation entry
+// For callers that must not allocate GPU memory when they simulate.  All
+// working state of sr_run_noalloc lives in this fixed array, which every GPU
+// that loads the library holds until the process exits.  Host code never uses
+// the symbol itself as an address: it asks the runtime for the device address
+// once per device (see noalloc_scratch).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocCap = 64;       // boundary events per region edge per iteration
+constexpr int kNoallocRing = 64;      // presimulated pairs per region
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices];     // device address of the scratch, per device
+
+// Device address of the scratch on the current device, looked up on first use.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SR_ECUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return SR_ECUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SR_OK;
+}
+
+// Carve a 256-byte-aligned piece of `bytes` out of the scratch.
+struct Carver {
+  unsigned char* base;
+  size_t used;
+  template <class T>
+  T* take(size_t count) {
+    used = (used + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + used);
+    used += count * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w, int region_h,
+                              uint64_t seed, const int8_t* spins_in, double Tw, int n_windows,
+                              int8_t* spins_out, uint64_t* counts_out, void* stream) {
+  if (L < 3 || region_w < 1 || region_h < 1 || L % region_w || L % region_h) return SR_EINVAL;
+  if (!(T > 0.0) || !std::isfinite(J) || !std::isfinite(h) || std::isnan(T)) return SR_EINVAL;
+  if (!(Tw > 0.0) || !std::isfinite(Tw) || n_windows < 1 || !spins_out) return SR_EINVAL;
+  if (region_w > 32 || region_h > 32) return SR_EUNSUPPORTED;
+
+  // the same context a sr_create_ex would build, without any allocation
+  sr_ctx c;
+  std::memset(&c, 0, sizeof c);
+  c.prm.L = L;
+  c.prm.J = J;
+  c.prm.h = h;
+  c.prm.T = T;
+  c.prm.region_w = region_w;
+  c.prm.region_h = region_h;
+  c.prm.seed = seed;
+  c.prm.init_mode = SR_INIT_FAIR_COIN;
+  c.prm.rates = SR_RATES_METROPOLIS;
+  c.prm.max_iters = 1 << 16;
+  c.prm.barrier_timeout_ms = 2000;
+  c.prm.test_barrier_skip_block = -1;
+  c.NX = L / region_w;
+  c.NY = L / region_h;
+  c.NR = c.NX * c.NY;
+  c.F = 63 - bitlen((long long)region_w * region_h);
+  c.scale = std::ldexp(1.0, -c.F);
+  rate_table(c.prm, c.F, c.P);
+  c.stream = (cudaStream_t)stream;
+
+  // size check before touching the GPU
+  const size_t nr = (size_t)c.NR, H = (size_t)region_h;
+  Carver probe{nullptr, 0};
+  probe.take<uint32_t>(2 * H * nr);               // rows
+  probe.take<uint32_t>(4 * nr);                   // halos
+  for (int a = 0; a < 7; ++a) probe.take<double>(2 * nr);   // carry
+  probe.take<double>((size_t)2 * 4 * kNoallocCap * nr);     // list times
+  probe.take<uint8_t>((size_t)2 * 4 * kNoallocCap * nr);    // list positions
+  probe.take<uint32_t>(2 * 4 * nr);               // list lengths
+  probe.take<double>((size_t)kNoallocRing * nr);  // ring x
+  probe.take<unsigned long long>((size_t)kNoallocRing * nr);  // ring V
+  probe.take<unsigned long long>(nr);             // ring ends
+  probe.take<DevStats>(1);
+  probe.take<uint32_t>(kWinRing);
+  if (probe.used > (size_t)SR_NOALLOC_SCRATCH_BYTES) return SR_ETOOLARGE;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c.clock_khz, cudaDevAttrClockRate, dev) != cudaSuccess)
+    return SR_ECUDA;
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc != SR_OK) return rc;
+  Carver cv{(unsigned char*)base, 0};
+  c.rows = cv.take<uint32_t>(2 * H * nr);
+  c.halo = cv.take<uint32_t>(4 * nr);
+  c.ci = cv.take<unsigned long long>(2 * nr);
+  c.cx = cv.take<double>(2 * nr);
+  c.ckv = cv.take<unsigned long long>(2 * nr);
+  c.cb = cv.take<double>(2 * nr);
+  c.ct = cv.take<double>(2 * nr);
+  c.cim = cv.take<double>(2 * nr);
+  c.cib = cv.take<double>(2 * nr);
+  c.ht = cv.take<double>((size_t)2 * 4 * kNoallocCap * nr);
+  c.hp = cv.take<uint8_t>((size_t)2 * 4 * kNoallocCap * nr);
+  c.hl = cv.take<uint32_t>(2 * 4 * nr);
+  c.rx = cv.take<double>((size_t)kNoallocRing * nr);
+  c.rkv = cv.take<unsigned long long>((size_t)kNoallocRing * nr);
+  c.rhi = cv.take<unsigned long long>(nr);
+  c.st = cv.take<DevStats>(1);
+  c.win_iters = cv.take<uint32_t>(kWinRing);
+  c.cap = kNoallocCap;
+  c.K = kNoallocRing;
+  c.Kcap = kNoallocRing;
+
+  // launch shape as sr_create_ex chooses it
+  const int per_sm = (c.NR + c.num_sms - 1) / c.num_sms;
+  const int bps = (per_sm + 255) / 256;
+  int rl = (per_sm + bps - 1) / bps;
+  if (rl > 32) rl = ((rl + 31) / 32) * 32;
+  if (rl > 256) rl = 256;
+  if (rl < 1) rl = 1;
+  int tpb = ((rl + 31) / 32) * 32;
+  if (tpb < 128) tpb = 128;
+  c.rl = rl;
+  c.tpb = tpb;
+  c.smem = (size_t)(region_h + 10) * rl * sizeof(uint32_t);
+  int per_sm_blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel, tpb, c.smem) !=
+          cudaSuccess ||
+      per_sm_blocks < 1)
+    return SR_EUNSUPPORTED;
+  int blocks = (c.NR + rl - 1) / rl;
+  if (blocks > per_sm_blocks * c.num_sms) blocks = per_sm_blocks * c.num_sms;
+  c.blocks = blocks;
+
+  // the shared scratch keeps the previous call's contents: start from zero
+  // where the kernels expect it (counters, barrier, flags, list lengths, rings)
+  if (cudaMemsetAsync(c.hl, 0, 2 * 4 * nr * sizeof(uint32_t), c.stream) != cudaSuccess)
+    return SR_ECUDA;
+  rc = init_state(&c, spins_in);            // spins, halos, clocks, counters, rings
+  if (rc != SR_OK) return rc;
+
+  // one persistent launch for all windows, then read the status word
+  KParams k = make_params(&c);
+  k.t0 = 0.0;
+  k.Tw = Tw;
+  k.nwin = n_windows;
+  if (cudaMemsetAsync(c.st, 0, offsetof(DevStats, cidx), c.stream) != cudaSuccess) return SR_ECUDA;
+  void* args[] = {&k};
+  if (cudaLaunchCooperativeKernel((const void*)relax_kernel, dim3(c.blocks), dim3(c.tpb), args,
+                                  c.smem, c.stream) != cudaSuccess)
+    return SR_ECUDA;
+  DevStats hs;
+  if (cudaMemcpyAsync(&hs, c.st, sizeof hs, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+      cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return SR_ECUDA;
+  if (hs.status & ST_TIMEOUT) return SR_TIMEOUT;
+  if (hs.status & ST_NOT_CONVERGED) return SR_NOT_CONVERGED;
+  if (hs.status & ST_CAPACITY) return SR_CAPACITY;
+  if (hs.status != 0u || (int)hs.windows_done != n_windows) return SR_ECUDA;
+
+  // outputs
+  unpack_rows_kernel<<<(unsigned)(((size_t)L * L + 255) / 256), 256, 0, c.stream>>>(k, hs.cidx,
+                                                                                    spins_out);
+  if (cudaGetLastError() != cudaSuccess) return SR_ECUDA;
+  if (counts_out &&
+      cudaMemcpyAsync(counts_out, c.ci + (size_t)hs.cidx * nr, nr * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToDevice, c.stream) != cudaSuccess)
+    return SR_ECUDA;
+  return cuda_rc(cudaStreamSynchronize(c.stream));
+}
