@@ -48,6 +48,7 @@ struct DevStats {
   unsigned max_win_events;      // most events one region committed in one window
   unsigned pad1;
   unsigned long long committed, generated, breaks, windows, iterations;
+  unsigned long long region_passes, region_skips;   // region iterations run / skipped
 };
 
 constexpr int kWinRing = 4096;
@@ -70,6 +71,7 @@ struct KParams {
   double* ht;                   // [2][4][cap][NR] boundary history: times
   uint8_t* hp;                  // [2][4][cap][NR] boundary history: positions along the edge
   uint32_t* hl;                 // [2][4][NR]   boundary history lengths
+  uint8_t* chg;                 // [2][NR]      lists of the iteration of that parity changed
   int cap;
   double* trt;                  // [NR][tcap]   committed event times (optional)
   uint32_t* trs;                // [NR][tcap]   committed event sites
@@ -203,7 +205,7 @@ __device__ __forceinline__ void move_class(const Region& g, const KParams& p, in
 
 // ---------------------------------------------------------------- region pass
 struct Acc {
-  unsigned long long events, breaks;
+  unsigned long long events, breaks, passes, skips;
   unsigned fmax, emax;
   bool changed, overflow;
 };
@@ -213,12 +215,50 @@ struct Acc {
 // merges the neighbours' previous-iteration boundary lists as break points,
 // writes the tentative end state to copy cidx ^ 1 and its own boundary lists to
 // parity wp, comparing them with its lists of the previous iteration.
-__device__ void run_region(const KParams& p, int r, int wp, unsigned cidx, double t_s, double t_end,
-                           Region& g, Acc& acc) {
+__device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, double t_s,
+                           double t_end, Region& g, Acc& acc) {
   const int W = p.W, H = p.H, NR = p.NR;
+  const int wp = n_iter & 1;
   const int rp = wp ^ 1;
   const int rx = r % p.NX, ry = r / p.NX;
   const size_t nr = (size_t)NR;
+  const size_t cap = (size_t)p.cap;
+
+  // ---- neighbours: d = 0 N, 1 S, 2 W, 3 E
+  const int qN = ((ry + p.NY - 1) % p.NY) * p.NX + rx;
+  const int qS = ((ry + 1) % p.NY) * p.NX + rx;
+  const int qW = ry * p.NX + (rx + p.NX - 1) % p.NX;
+  const int qE = ry * p.NX + (rx + 1) % p.NX;
+  int q[4] = {qN, qS, qW, qE};
+  bool has[4] = {!g.spans_y, !g.spans_y, !g.spans_x, !g.spans_x};
+
+  // ---- a region whose neighbours' lists did not change in the last iteration
+  // sees the same input as then, so its output is the same: keep the
+  // tentative state and carry the lists over instead of replaying the window
+  if (n_iter >= 2) {
+    bool dirty = false;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (has[d] && __ldcg(&p.chg[(size_t)rp * nr + q[d]])) dirty = true;
+    if (!dirty) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (!has[e]) continue;
+        const unsigned n = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
+        for (unsigned j = 0; j < n; ++j) {
+          const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
+          const size_t dst = (((size_t)wp * 4 + e) * cap + j) * nr + r;
+          p.ht[dst] = __ldcg(&p.ht[src]);
+          p.hp[dst] = __ldcg(&p.hp[src]);
+        }
+        p.hl[((size_t)wp * 4 + e) * nr + r] = n;
+      }
+      p.chg[(size_t)wp * nr + r] = 0;
+      acc.skips += 1;
+      return;
+    }
+  }
+  acc.passes += 1;
 
   // ---- committed state
   const uint32_t* rows_c = p.rows + (size_t)cidx * H * nr;
@@ -271,17 +311,10 @@ __device__ void run_region(const KParams& p, int r, int wp, unsigned cidx, doubl
     lam += (unsigned long long)Nk[k] * p.P[k];
   }
 
-  // ---- incoming boundary lists: the neighbours' lists of the previous iteration
-  // d = 0 N, 1 S, 2 W, 3 E; my N halo is fed by the N neighbour's S list, etc.
-  const int qN = ((ry + p.NY - 1) % p.NY) * p.NX + rx;
-  const int qS = ((ry + 1) % p.NY) * p.NX + rx;
-  const int qW = ry * p.NX + (rx + p.NX - 1) % p.NX;
-  const int qE = ry * p.NX + (rx + 1) % p.NX;
+  // ---- incoming boundary lists: the neighbours' lists of the previous iteration;
+  // my N halo is fed by the N neighbour's S list, etc.
   const double INF = __longlong_as_double(0x7FF0000000000000ll);
-  const size_t cap = (size_t)p.cap;
-  int q[4] = {qN, qS, qW, qE};
   const int ein[4] = {1, 0, 3, 2};
-  bool has[4] = {!g.spans_y, !g.spans_y, !g.spans_x, !g.spans_x};
   unsigned len[4], idx[4];
   double nt[4];
   unsigned npos[4];
@@ -477,6 +510,7 @@ __device__ void run_region(const KParams& p, int r, int wp, unsigned cidx, doubl
       p.hl[((size_t)wp * 4 + e) * nr + r] = olen[e];
     }
   }
+  p.chg[(size_t)wp * nr + r] = (changed || overflow) ? 1 : 0;
   // ---- tentative end state
   const unsigned tc = cidx ^ 1u;
   uint32_t* rows_t = p.rows + (size_t)tc * H * nr;
@@ -595,15 +629,16 @@ __global__ void __launch_bounds__(256) relax_kernel(KParams p) {
     for (; n <= p.max_iters; ++n) {
       const unsigned slot = giter % 3u;
       ++giter;
-      const int wp = n & 1;
-      Acc acc = {0ull, 0ull, 0u, 0u, false, false};
-      for (int r = gtid; r < p.NR; r += gthreads) run_region(p, r, wp, cidx, t_s, t_end, g, acc);
+      Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, false, false};
+      for (int r = gtid; r < p.NR; r += gthreads) run_region(p, r, n, cidx, t_s, t_end, g, acc);
       if (acc.changed) atomicOr(&st->flags[slot], 1u);
       if (acc.overflow) atomicOr(&st->status, ST_CAPACITY);
       if (acc.events) atomicAdd(&st->generated, acc.events);
       if (acc.breaks) atomicAdd(&st->breaks, acc.breaks);
       if (acc.fmax) atomicMax(&st->max_f, acc.fmax);
       if (acc.emax) atomicMax(&st->max_win_events, acc.emax);
+      if (acc.passes) atomicAdd(&st->region_passes, acc.passes);
+      if (acc.skips) atomicAdd(&st->region_skips, acc.skips);
       if (!grid_barrier(st, p.timeout_cycles)) return;
       if (blockIdx.x == 0 && threadIdx.x == 0) st->flags[(slot + 2u) % 3u] = 0u;
       if (*(volatile unsigned*)&st->status & ST_CAPACITY) return;   // window not committed
@@ -784,6 +819,7 @@ struct sr_ctx {
   int num_sms;
   int clock_khz;
   uint32_t *rows, *halo, *hl, *trs, *win_iters;
+  uint8_t* chg;
   unsigned long long *ci, *ckv, *rkv, *rhi;
   double* rx;
   int K, Kcap;
@@ -860,6 +896,7 @@ KParams make_params(const sr_ctx* c) {
   k.ht = c->ht;
   k.hp = c->hp;
   k.hl = c->hl;
+  k.chg = c->chg;
   k.cap = c->cap;
   k.trt = c->trt;
   k.trs = c->trs;
@@ -963,7 +1000,7 @@ int set_ring(sr_ctx* c, int K) {
 void free_all(sr_ctx* c) {
   void* dev[] = {c->rows, c->halo, c->hl, c->trs, c->win_iters, c->ci, c->ckv, c->cx, c->cb,
                  c->ct, c->cim, c->cib, c->ht, c->trt, c->hp, c->st, c->obs_i, c->obs_f, c->stage,
-                 c->rx, c->rkv, c->rhi};
+                 c->rx, c->rkv, c->rhi, c->chg};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (c->h_st) cudaFreeHost(c->h_st);
@@ -1087,6 +1124,7 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   rc |= dalloc(&c->obs_f, 2);
   rc |= dalloc(&c->stage, (size_t)p.L * p.L);
   rc |= dalloc(&c->rhi, nr);
+  rc |= dalloc(&c->chg, 2 * nr);
   if (p.trace_capacity > 0) {
     rc |= dalloc(&c->trt, nr * (size_t)p.trace_capacity);
     rc |= dalloc(&c->trs, nr * (size_t)p.trace_capacity);
@@ -1432,6 +1470,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   probe.take<double>((size_t)2 * 4 * kNoallocCap * nr);     // list times
   probe.take<uint8_t>((size_t)2 * 4 * kNoallocCap * nr);    // list positions
   probe.take<uint32_t>(2 * 4 * nr);               // list lengths
+  probe.take<uint8_t>(2 * nr);                    // list-changed flags
   probe.take<double>((size_t)kNoallocRing * nr);  // ring x
   probe.take<unsigned long long>((size_t)kNoallocRing * nr);  // ring V
   probe.take<unsigned long long>(nr);             // ring ends
@@ -1460,6 +1499,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.ht = cv.take<double>((size_t)2 * 4 * kNoallocCap * nr);
   c.hp = cv.take<uint8_t>((size_t)2 * 4 * kNoallocCap * nr);
   c.hl = cv.take<uint32_t>(2 * 4 * nr);
+  c.chg = cv.take<uint8_t>(2 * nr);
   c.rx = cv.take<double>((size_t)kNoallocRing * nr);
   c.rkv = cv.take<unsigned long long>((size_t)kNoallocRing * nr);
   c.rhi = cv.take<unsigned long long>(nr);
