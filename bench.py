@@ -145,7 +145,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     seed = 1 + rank
     stream = torch.cuda.current_stream()
-    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed)
+    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def one_pass(record):
@@ -212,7 +212,7 @@ def run_ours(args):
     rng = np.random.default_rng(1000 + rank)
     init_host = torch.from_numpy(np.where(rng.random((L, L)) < 0.5, 1, -1).astype(np.int8)).pin_memory()
     out_host = torch.empty((L, L), dtype=torch.int8).pin_memory()
-    e2e_lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed)
+    e2e_lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr)
     e2e_committed, e2e_time = 0, 0.0
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -261,7 +261,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded fair-coin lattice)",
         "config": {"workload": WORKLOAD, "regions": lat.n_regions,
-                   "launch": {"threads_per_block": lat.threads_per_block, "blocks": lat.blocks},
+                   "launch": {"region_slots_per_block": lat.threads_per_block, "blocks": lat.blocks,
+                              "lanes_per_region": args.lpr or "auto"},
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "per_window_length": tw_detail},
@@ -292,17 +293,26 @@ def run_profile_case(args):
 
     import paper_cs_0405053_gb300 as sr
     torch.cuda.set_device(0)
-    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=1)
+    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=1, lanes_per_region=args.lpr)
+    t0 = None
     for _ in range(args.warmup):
         lat.reset()
         lat.run_windows(args.tw, args.windows)
     lat.reset()
-    lat.run_windows(args.tw, args.windows)
-    o = lat.observables()
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.run_windows(args.tw, args.windows)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    o = lat.observables()
+    mhz = 2070.0
     print(json.dumps({"profile_case": True, "tw": args.tw, "windows": args.windows,
+                      "lanes_per_region": args.lpr, "ms": dt * 1e3,
                       "committed": o.committed, "generated": o.generated,
-                      "iterations": o.iterations}))
+                      "iterations": o.iterations, "passes": o.region_passes,
+                      "skips": o.region_skips,
+                      "busy_ms_mean": o.run_cycles / max(1, o.slots) / mhz / 1e3,
+                      "busy_ms_max": o.run_cycles_max / mhz / 1e3, "slots": o.slots}))
     return 0
 
 
@@ -316,6 +326,8 @@ def main():
                     help="run only a short slice of the workload (for ncu)")
     ap.add_argument("--tw", type=float, default=1.0)
     ap.add_argument("--windows", type=int, default=5)
+    ap.add_argument("--lpr", type=int, default=0,
+                    help="lanes per region: 1, 32 or 0 (automatic)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

@@ -68,7 +68,10 @@ typedef struct sr_params {
                                    (grows by doubling when exceeded, see sr_run_windows) */
   int max_iters;                /* iteration cap per window; 0 = 1<<16 */
   int trace_capacity;           /* committed events recorded per region; 0 = no trace */
-  int threads_per_block;        /* region lanes per block (one region per lane); 0 = automatic */
+  int lanes_per_region;         /* 1 = one lane per region, 32 = one warp per region,
+                                   0 = automatic (a warp while the regions fit the resident warps) */
+  int threads_per_block;        /* region slots per block (lanes, or warps with a warp per
+                                   region); 0 = automatic */
   int block_threads;            /* threads per block, >= region lanes; the extra threads help
                                    draw the presimulated random pairs; 0 = automatic */
   int blocks;                   /* 0 = automatic (all regions resident if they fit) */
@@ -97,6 +100,11 @@ typedef struct sr_obs {
                                    iteration (f of §6) */
   uint32_t capacity;            /* current history capacity per edge */
   uint64_t launches;            /* kernels this context has launched since creation */
+  uint64_t region_passes;       /* region iterations replayed */
+  uint64_t region_skips;        /* region iterations skipped (inputs unchanged) */
+  uint64_t run_cycles;          /* SM cycles region slots spent on their regions, summed */
+  uint64_t run_cycles_max;      /* the same for the busiest slot */
+  uint64_t slots;               /* region slots (lanes or warps) that reported */
 } sr_obs;
 
 /* Create a context with Metropolis rates, fair-coin initial spins and
@@ -187,6 +195,14 @@ int sr_get_info(sr_ctx* ctx, int* n_regions, int* frac_bits, uint64_t* P, int* t
  * Host arrays of n entries; either may be NULL.  Blocks until done.  Errors:
  * SR_EINVAL, SR_ENOMEM, SR_ECUDA. */
 int sr_eval_draws(uint64_t seed, uint32_t region, uint64_t i0, size_t n, double* x, uint64_t* kV);
+
+/* Evaluate on the GPU the integer-emulated IEEE double operations used by the
+ * time formula of the event loop (Eqs. 3.4, 5.2-5.6): op 0 a+b, 1 a-b,
+ * 2 a*b, 3 a/b (operands >= 0, b > 0 for division), 4 a converted from an
+ * unsigned integer (bits of a) times 2^-F with F = (int)b.  out[i] receives the
+ * result for a[i], b[i].  Host arrays of n doubles.  Blocks until done.  Errors:
+ * SR_EINVAL, SR_ENOMEM, SR_ECUDA. */
+int sr_eval_softfloat(int op, const double* a, const double* b, double* out, size_t n);
 
 /* Run a whole simulation without allocating any memory.  The paper has no
  * counterpart: this exists for callers that cannot allocate GPU memory at the

@@ -37,7 +37,7 @@ class _Params(C.Structure):
                 ("region_w", C.c_int), ("region_h", C.c_int), ("seed", C.c_uint64),
                 ("init_mode", C.c_int), ("rates", C.c_int), ("capacity", C.c_int),
                 ("max_iters", C.c_int), ("trace_capacity", C.c_int),
-                ("threads_per_block", C.c_int), ("block_threads", C.c_int), ("blocks", C.c_int),
+                ("lanes_per_region", C.c_int), ("threads_per_block", C.c_int), ("block_threads", C.c_int), ("blocks", C.c_int),
                 ("barrier_timeout_ms", C.c_int), ("test_barrier_skip_block", C.c_int),
                 ("stream", C.c_void_p)]
 
@@ -48,7 +48,9 @@ class _Obs(C.Structure):
                 ("committed", C.c_uint64), ("generated", C.c_uint64), ("breaks", C.c_uint64),
                 ("windows", C.c_uint64), ("iterations", C.c_uint64), ("last_iters", C.c_uint32),
                 ("max_iters_seen", C.c_uint32), ("max_f", C.c_uint32), ("capacity", C.c_uint32),
-                ("launches", C.c_uint64)]
+                ("launches", C.c_uint64), ("region_passes", C.c_uint64),
+                ("region_skips", C.c_uint64), ("run_cycles", C.c_uint64),
+                ("run_cycles_max", C.c_uint64), ("slots", C.c_uint64)]
 
 
 @dataclass
@@ -70,6 +72,11 @@ class Observables:
     max_f: int
     capacity: int
     launches: int
+    region_passes: int
+    region_skips: int
+    run_cycles: int
+    run_cycles_max: int
+    slots: int
 
 
 _lib = None
@@ -104,6 +111,7 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_get_window_iters": (C.c_int, [_P, _P, C.c_size_t]),
             "sr_eval_draws": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint64, C.c_size_t, _P, _P]),
             "sr_get_info": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+            "sr_eval_softfloat": (C.c_int, [C.c_int, _P, _P, _P, C.c_size_t]),
             "sr_strerror": (C.c_char_p, [C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -141,13 +149,23 @@ def eval_draws(seed: int, region: int, i0: int, n: int) -> Tuple[np.ndarray, np.
     return x, kv
 
 
+def eval_softfloat(op: int, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """The integer-emulated double operation `op` of the event loop, on the GPU."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.zeros_like(a)
+    _check(library().sr_eval_softfloat(op, _ptr(a), _ptr(b), _ptr(out), a.size), "sr_eval_softfloat")
+    return out
+
+
 class Lattice:
     """One L x L periodic lattice split into region_w x region_h regions."""
 
     def __init__(self, L: int, J: float = 1.0, h: float = 0.0, T: float = 1.0,
                  region: Tuple[int, int] = (16, 16), seed: int = 1, init: str = "fair",
                  rates: str = "metropolis", capacity: int = 0, max_iters: int = 0,
-                 trace_capacity: int = 0, threads_per_block: int = 0, block_threads: int = 0,
+                 trace_capacity: int = 0, lanes_per_region: int = 0, threads_per_block: int = 0,
+                 block_threads: int = 0,
                  blocks: int = 0,
                  barrier_timeout_ms: int = 0, test_barrier_skip_block: int = -1,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
@@ -159,7 +177,8 @@ class Lattice:
         self.seed = seed
         self.trace_capacity = trace_capacity
         prm = _Params(L, J, h, T, region[0], region[1], seed, INIT_MODES[init], RATES[rates],
-                      capacity, max_iters, trace_capacity, threads_per_block, block_threads, blocks,
+                      capacity, max_iters, trace_capacity, lanes_per_region, threads_per_block,
+                      block_threads, blocks,
                       barrier_timeout_ms, test_barrier_skip_block, stream)
         self._ctx = _P()
         _check(lib.sr_create_ex(C.byref(self._ctx), C.byref(prm)), "sr_create_ex")

@@ -26,6 +26,7 @@
 
 #include "sr.h"
 #include "sr_device.cuh"
+#include "sr_softfloat.cuh"
 
 namespace sr {
 
@@ -49,6 +50,8 @@ struct DevStats {
   unsigned pad1;
   unsigned long long committed, generated, breaks, windows, iterations;
   unsigned long long region_passes, region_skips;   // region iterations run / skipped
+  unsigned long long run_cycles, run_cycles_max;    // cycles region slots spent on their regions
+  unsigned long long slots;                         // region slots that reported
 };
 
 constexpr int kWinRing = 4096;
@@ -536,6 +539,495 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
   acc.overflow |= overflow;
 }
 
+// ---------------------------------------------------------------- warp per region
+// The same region pass with one warp per region: lane y holds row y in a
+// register, the ten class counts sit in lanes 0..9, the four incoming-list
+// cursors in lanes 0..3.  Class choice (Eqs. 3.5-3.6) is a warp prefix scan of
+// N_k p_k and a ballot; site choice (Eqs. 3.7-3.8) a prefix scan of the rows'
+// class-k* counts and a ballot; the waiting time (Eqs. 3.4, 5.2-5.6) runs in
+// integer-emulated IEEE doubles (sr_softfloat.cuh), identical bits to the
+// lane version.  Control flow is uniform across the warp.
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int src) {
+  const unsigned lo = __shfl_sync(kFull, (unsigned)v, src);
+  const unsigned hi = __shfl_sync(kFull, (unsigned)(v >> 32), src);
+  return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ unsigned long long shfl_up_u64(unsigned long long v, int d) {
+  const unsigned lo = __shfl_up_sync(kFull, (unsigned)v, d);
+  const unsigned hi = __shfl_up_sync(kFull, (unsigned)(v >> 32), d);
+  return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ long long shfl_xor_s64(long long v, int m) {
+  const unsigned lo = __shfl_xor_sync(kFull, (unsigned)v, m);
+  const unsigned hi = __shfl_xor_sync(kFull, (unsigned)((unsigned long long)v >> 32), m);
+  return (long long)(((unsigned long long)hi << 32) | lo);
+}
+
+// tau of Eq. 3.4 / 5.6 in integer-emulated doubles (same bits as tau_hat).
+__device__ __forceinline__ double tau_soft(double t_last, double x, double b, unsigned long long lam,
+                                           int F) {
+  if (lam == 0ull) return __longlong_as_double(0x7FF0000000000000ll);
+  double d = sf::sub_pos(x, b);
+  if (d < 0.0) d = 0.0;
+  const double t = sf::add_pos(t_last, sf::div_pos(d, sf::u64_scaled(lam, F)));
+  if (__double_as_longlong(t) <= __double_as_longlong(t_last))
+    return __longlong_as_double(__double_as_longlong(t_last) + 1ll);
+  return t;
+}
+
+// 128-bit signed accumulator of fixed-point times (observables).
+struct Acc128 {
+  unsigned long long lo;
+  long long hi;
+  __device__ __forceinline__ void add(long long k, unsigned long long v) {   // += k * v, |k| <= 2
+    unsigned long long a = v;
+    if (k == 2 || k == -2) a = v << 1;
+    const long long ahi = (k == 2 || k == -2) ? (long long)(v >> 63) : 0;
+    if (k > 0) {
+      const unsigned long long n = lo + a;
+      hi += ahi + (n < lo ? 1 : 0);
+      lo = n;
+    } else if (k < 0) {
+      const unsigned long long n = lo - a;
+      hi -= ahi + (lo < a ? 1 : 0);
+      lo = n;
+    }
+  }
+  __device__ __forceinline__ double value(int frac) const {   // as a double times 2^-frac
+    return __dadd_rn(__dmul_rn((double)hi, __longlong_as_double((long long)(1023 + 64 - frac) << 52)),
+                     __dmul_rn(__ull2double_rn(lo), __longlong_as_double((long long)(1023 - frac) << 52)));
+  }
+};
+
+// t >= 0 as an integer multiple of 2^-frac (truncated), t * 2^frac < 2^63.
+__device__ __forceinline__ unsigned long long to_fixed(double t, int frac) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  if (b == 0ull) return 0ull;
+  const int e = (int)(b >> 52) - 1075 + frac;       // t = m 2^(ebits - 1075)
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  if (e >= 0) return m << e;
+  if (e <= -64) return 0ull;
+  return m >> (-e);
+}
+
+__device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned cidx, double t_s,
+                                double t_end, Acc& acc) {
+  const int lane = threadIdx.x & 31;
+  const int W = p.W, H = p.H;
+  const size_t nr = (size_t)p.NR;
+  const size_t cap = (size_t)p.cap;
+  const int wp = n_iter & 1, rp = wp ^ 1;
+  const int rx = r % p.NX, ry = r / p.NX;
+  const bool spx = p.spans_x != 0, spy = p.spans_y != 0;
+  const uint32_t wmask = (W == 32) ? 0xFFFFFFFFu : ((1u << W) - 1u);
+  const bool vlane = lane < H;
+  const bool has_y = !spy, has_x = !spx;
+  const double INF = __longlong_as_double(0x7FF0000000000000ll);
+
+  // lane d < 4 serves direction d (0 N, 1 S, 2 W, 3 E)
+  int qd = 0;
+  if (lane == 0) qd = ((ry + p.NY - 1) % p.NY) * p.NX + rx;
+  else if (lane == 1) qd = ((ry + 1) % p.NY) * p.NX + rx;
+  else if (lane == 2) qd = ry * p.NX + (rx + p.NX - 1) % p.NX;
+  else if (lane == 3) qd = ry * p.NX + (rx + 1) % p.NX;
+  const bool hasd = (lane < 2 && has_y) || (lane >= 2 && lane < 4 && has_x);
+
+  // ---- skip when no neighbour's lists changed in the last iteration
+  if (n_iter >= 2) {
+    const bool dirty = hasd && __ldcg(&p.chg[(size_t)rp * nr + qd]) != 0;
+    if (!__any_sync(kFull, dirty)) {
+      for (int e = 0; e < 4; ++e) {
+        if (!((e < 2) ? has_y : has_x)) continue;
+        const unsigned n = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
+        for (unsigned j = lane; j < n; j += 32) {
+          const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
+          const size_t dst = (((size_t)wp * 4 + e) * cap + j) * nr + r;
+          p.ht[dst] = __ldcg(&p.ht[src]);
+          p.hp[dst] = __ldcg(&p.hp[src]);
+        }
+        if (lane == 0) p.hl[((size_t)wp * 4 + e) * nr + r] = n;
+      }
+      if (lane == 0) {
+        p.chg[(size_t)wp * nr + r] = 0;
+        acc.skips += 1;
+      }
+      return;
+    }
+  }
+  if (lane == 0) acc.passes += 1;
+
+  // ---- committed state
+  uint32_t row = vlane ? __ldcg(&p.rows[((size_t)cidx * H + lane) * nr + r]) : 0u;
+  uint32_t hN = __ldcg(&p.halo[0 * nr + r]), hS = __ldcg(&p.halo[1 * nr + r]);
+  uint32_t hW = __ldcg(&p.halo[2 * nr + r]), hE = __ldcg(&p.halo[3 * nr + r]);
+  unsigned long long i = __ldcg(&p.ci[cidx * nr + r]);
+  double x = __ldcg(&p.cx[cidx * nr + r]);
+  unsigned long long kv = __ldcg(&p.ckv[cidx * nr + r]);
+  double b = __ldcg(&p.cb[cidx * nr + r]);
+  double tl = __ldcg(&p.ct[cidx * nr + r]);
+  const unsigned long long hi_ring = __ldcg(&p.rhi[r]);
+  const unsigned long long kmask = (unsigned long long)p.K - 1ull;
+  double px = 0.0;
+  unsigned long long pkv = 0ull;
+  bool pvalid = (i + 1ull) < hi_ring;
+  if (pvalid) {
+    const size_t a = (size_t)((i + 1ull) & kmask) * nr + r;
+    px = __ldcg(&p.rx[a]);
+    pkv = __ldcg(&p.rkv[a]);
+  }
+  int F = 0;
+  {
+    unsigned long long sc = (unsigned long long)__double_as_longlong(p.scale);
+    F = 1023 - (int)(sc >> 52);
+  }
+
+  // neighbour words and per-position up counts of my row
+  uint32_t s0, s1, s2;
+  auto refresh = [&]() {
+    const uint32_t vu = __shfl_sync(kFull, row, lane > 0 ? lane - 1 : H - 1);
+    const uint32_t vd = __shfl_sync(kFull, row, lane < H - 1 ? lane + 1 : 0);
+    const uint32_t up = (lane > 0 || spy) ? vu : hN;
+    const uint32_t dn = (lane < H - 1 || spy) ? vd : hS;
+    const uint32_t lb = spx ? (row >> (W - 1)) & 1u : (hW >> lane) & 1u;
+    const uint32_t rb = spx ? (row & 1u) : (hE >> lane) & 1u;
+    const uint32_t lf = ((row << 1) | lb) & wmask;
+    const uint32_t rt = (row >> 1) | (rb << (W - 1));
+    add4(up, dn, lf, rt, s0, s1, s2);
+  };
+  refresh();
+
+  // ---- class counts (lane k holds N_k) and Lambda
+  unsigned myN = 0;
+  unsigned long long lam = 0ull;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const uint32_t e = vlane ? (eq_count(s0, s1, s2, k % 5) & (k >= 5 ? row : ~row) & wmask) : 0u;
+    const unsigned tot = __reduce_add_sync(kFull, (unsigned)__popc(e));
+    if (lane == k) myN = tot;
+    lam += (unsigned long long)tot * p.P[k];
+  }
+  int mag0 = 0, bond0 = 0;
+  {
+    const uint32_t vd = __shfl_sync(kFull, row, lane < H - 1 ? lane + 1 : 0);
+    const uint32_t dn = (lane < H - 1 || spy) ? vd : hS;
+    const uint32_t rb = spx ? (row & 1u) : (hE >> lane) & 1u;
+    const uint32_t rt = (row >> 1) | (rb << (W - 1));
+    const int m = vlane ? 2 * __popc(row) - W : 0;
+    const int bd = vlane ? (W - 2 * __popc((row ^ rt) & wmask)) + (W - 2 * __popc((row ^ dn) & wmask)) : 0;
+    mag0 = __reduce_add_sync(kFull, m);
+    bond0 = __reduce_add_sync(kFull, bd);
+  }
+
+  // ---- incoming cursors (lane d), two entries buffered
+  const int ein = (lane == 0) ? 1 : (lane == 1) ? 0 : (lane == 2) ? 3 : 2;
+  unsigned len = 0, idx = 0, npos = 0, npos2 = 0;
+  double nt = INF, nt2 = INF;
+  if (hasd) {
+    len = __ldcg(&p.hl[((size_t)rp * 4 + ein) * nr + qd]);
+    if (len > 0) {
+      const size_t a = (((size_t)rp * 4 + ein) * cap) * nr + qd;
+      nt = __ldcg(&p.ht[a]);
+      npos = __ldcg(&p.hp[a]);
+    }
+    if (len > 1) {
+      const size_t a = (((size_t)rp * 4 + ein) * cap + 1) * nr + qd;
+      nt2 = __ldcg(&p.ht[a]);
+      npos2 = __ldcg(&p.hp[a]);
+    }
+  }
+
+  unsigned olen0 = 0, olen1 = 0, olen2 = 0, olen3 = 0;
+  bool overflow = false;
+  unsigned long long events = 0, brk = 0;
+  unsigned bevents = 0;
+  int ksig = 0, kbeta = 0;
+  const int frac = 62 - (int)((((unsigned long long)__double_as_longlong(t_end)) >> 52) - 1022);
+  Acc128 ssig = {0ull, 0}, sbeta = {0ull, 0};
+  const uint32_t gx0 = (uint32_t)(rx * W), gy0 = (uint32_t)(ry * H);
+
+  double tau = tau_soft(tl, x, b, lam, F);
+  for (;;) {
+    // earliest pending break point over the four cursor lanes
+    long long key = (lane < 4) ? __double_as_longlong(nt) : 0x7FF0000000000000ll;
+    int who = lane;
+#pragma unroll
+    for (int m = 1; m <= 2; m <<= 1) {
+      const long long ok = shfl_xor_s64(key, m);
+      const int ow = __shfl_xor_sync(kFull, who, m);
+      if (ok < key || (ok == key && ow < who)) {
+        key = ok;
+        who = ow;
+      }
+    }
+    key = (long long)shfl_u64((unsigned long long)key, 0);
+    who = __shfl_sync(kFull, who, 0);
+    const long long tau_b = __double_as_longlong(tau);
+
+    if (tau_b <= key) {
+      if (!(tau_b < __double_as_longlong(t_end))) break;
+      // ---- class k*: prefix sums A(k) of N_k p_k over lanes 0..9 (Eqs. 3.5-3.6)
+      const unsigned long long mV = 2ull * kv + 1ull;
+      const unsigned long long plo = mV * lam, phi = __umul64hi(mV, lam);
+      const unsigned long long q53 = (phi << 11) | (plo >> 53);
+      const bool exact = (plo & ((1ull << 53) - 1ull)) == 0ull;
+      const unsigned long long term = (lane < 10) ? (unsigned long long)myN * p.P[lane < 10 ? lane : 0] : 0ull;
+      unsigned long long A = term;
+#pragma unroll
+      for (int d = 1; d < 16; d <<= 1) {
+        const unsigned long long o = shfl_up_u64(A, d);
+        if (lane >= d) A += o;
+      }
+      const bool hit = lane < 10 && (q53 < A || (q53 == A && exact));
+      const int ks = __ffs(__ballot_sync(kFull, hit)) - 1;
+      const unsigned long long Aprev = shfl_u64(A - term, ks);
+      const unsigned Nks = __shfl_sync(kFull, myN, ks);
+      const unsigned long long Pk = p.P[ks];
+      // position in the class (Eqs. 3.7-3.8): floor((V Lambda - A(k*-1)) / p_k*)
+      const unsigned long long D = q53 - Aprev;
+      unsigned j = (unsigned)__float2uint_rz(__fdividef(__ull2float_rn(D), __ull2float_rn(Pk)));
+      if (j > Nks) j = Nks;
+#pragma unroll
+      for (int fix = 0; fix < 2; ++fix) {
+        if ((unsigned long long)j * Pk > D) --j;
+        else if ((unsigned long long)(j + 1) * Pk <= D) ++j;
+      }
+      if (j >= Nks) j = Nks - 1;
+      // the j-th class-k* site in row-major order
+      const int sp = ks >= 5;
+      const int nn = ks - 5 * sp;
+      const uint32_t mrow = vlane ? (eq_count(s0, s1, s2, nn) & (sp ? row : ~row) & wmask) : 0u;
+      const unsigned cnt = __popc(mrow);
+      unsigned cum = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned o = __shfl_up_sync(kFull, cum, d);
+        if (lane >= d) cum += o;
+      }
+      const int fy = __ffs(__ballot_sync(kFull, vlane && j < cum)) - 1;
+      const unsigned before = __shfl_sync(kFull, cum - cnt, fy);
+      const int fxl = nth_set_bit(mrow, j - before);
+      const int fx = __shfl_sync(kFull, fxl, fy);
+      const int s_old = (__shfl_sync(kFull, row, fy) >> fx) & 1;
+
+      // ---- classes before the flip of the site and its in-region neighbours
+      auto nup_at = [&](int xx) -> int {
+        return (int)(((s0 >> xx) & 1u) + 2u * ((s1 >> xx) & 1u) + 4u * ((s2 >> xx) & 1u));
+      };
+      // lane fy packs (v, left, right); its row neighbours pack (x*)
+      unsigned pk_mid = 0u, pk_vert = 0u;
+      if (lane == fy) {
+        const int cv = 5 * s_old + nup_at(fx);
+        pk_mid = (unsigned)cv | 0x10u;
+        if (fx > 0 || spx) {
+          const int xl = fx > 0 ? fx - 1 : W - 1;
+          pk_mid |= ((unsigned)(5 * ((row >> xl) & 1u) + nup_at(xl)) | 0x10u) << 5;
+        }
+        if (fx < W - 1 || spx) {
+          const int xr = fx < W - 1 ? fx + 1 : 0;
+          pk_mid |= ((unsigned)(5 * ((row >> xr) & 1u) + nup_at(xr)) | 0x10u) << 10;
+        }
+      }
+      const int yu = fy > 0 ? fy - 1 : H - 1;
+      const int yd = fy < H - 1 ? fy + 1 : 0;
+      const bool hu = fy > 0 || spy, hd = fy < H - 1 || spy;
+      if ((lane == yu && hu) || (lane == yd && hd))
+        pk_vert = ((unsigned)(5 * ((row >> fx) & 1u) + nup_at(fx))) | 0x10u;
+      const unsigned m_mid = __shfl_sync(kFull, pk_mid, fy);
+      const unsigned m_up = hu ? __shfl_sync(kFull, pk_vert, yu) : 0u;
+      const unsigned m_dn = hd ? __shfl_sync(kFull, pk_vert, yd) : 0u;
+      const int dnb = s_old ? -1 : 1;
+      int dN = 0;
+      long long dlam = 0;
+      auto apply = [&](unsigned code, int delta) {
+        if (!(code & 0x10u)) return;
+        const int from = (int)(code & 0xFu), to = from + delta;
+        dN += (lane == to) - (lane == from);
+        dlam += (long long)(p.P[to] - p.P[from]);
+      };
+      apply(m_mid & 0x1Fu, s_old ? -5 : 5);
+      apply((m_mid >> 5) & 0x1Fu, dnb);
+      apply((m_mid >> 10) & 0x1Fu, dnb);
+      apply(m_up, dnb);
+      apply(m_dn, dnb);
+      myN = (unsigned)((int)myN + dN);
+      lam = lam + (unsigned long long)dlam;
+      if (lane == fy) row ^= (1u << fx);
+
+      // ---- observables: dM = 2 sig, dBonds = 4 beta
+      const int sig = s_old ? -1 : 1;
+      const int nup_v = (int)(m_mid & 0xFu) - 5 * s_old;
+      const int beta = sig * (nup_v - 2);
+      const unsigned long long tfix = to_fixed(tau, frac);
+      ksig += sig;
+      ssig.add(sig, tfix);
+      kbeta += beta;
+      sbeta.add(beta, tfix);
+
+      // ---- boundary history (lane 0 writes; compared at the end)
+      bool boundary = false;
+      if (has_y && fy == 0) {
+        if (olen0 >= cap) overflow = true;
+        else if (lane == 0) {
+          const size_t a = (((size_t)wp * 4 + 0) * cap + olen0) * nr + r;
+          p.ht[a] = tau;
+          p.hp[a] = (uint8_t)fx;
+        }
+        ++olen0;
+        boundary = true;
+      }
+      if (has_y && fy == H - 1) {
+        if (olen1 >= cap) overflow = true;
+        else if (lane == 0) {
+          const size_t a = (((size_t)wp * 4 + 1) * cap + olen1) * nr + r;
+          p.ht[a] = tau;
+          p.hp[a] = (uint8_t)fx;
+        }
+        ++olen1;
+        boundary = true;
+      }
+      if (has_x && fx == 0) {
+        if (olen2 >= cap) overflow = true;
+        else if (lane == 0) {
+          const size_t a = (((size_t)wp * 4 + 2) * cap + olen2) * nr + r;
+          p.ht[a] = tau;
+          p.hp[a] = (uint8_t)fy;
+        }
+        ++olen2;
+        boundary = true;
+      }
+      if (has_x && fx == W - 1) {
+        if (olen3 >= cap) overflow = true;
+        else if (lane == 0) {
+          const size_t a = (((size_t)wp * 4 + 3) * cap + olen3) * nr + r;
+          p.ht[a] = tau;
+          p.hp[a] = (uint8_t)fy;
+        }
+        ++olen3;
+        boundary = true;
+      }
+      if (boundary) ++bevents;
+      if (lane == 0 && p.tcap > 0 && i < (unsigned long long)p.tcap) {
+        p.trt[(size_t)r * p.tcap + i] = tau;
+        p.trs[(size_t)r * p.tcap + i] = (gy0 + fy) * (uint32_t)p.L + gx0 + fx;
+      }
+      ++events;
+      if (overflow) break;
+      // ---- next event: clock restarts at tau with the next presimulated pair
+      tl = tau;
+      b = 0.0;
+      ++i;
+      if (pvalid) {
+        x = px;
+        kv = pkv;
+      } else {
+        draw_event(i, (uint32_t)r, p.key0, p.key1, x, kv);
+      }
+      pvalid = (i + 1ull) < hi_ring;
+      if (pvalid) {
+        const size_t a = (size_t)((i + 1ull) & kmask) * nr + r;
+        px = __ldcg(&p.rx[a]);
+        pkv = __ldcg(&p.rkv[a]);
+      }
+      refresh();
+    } else {
+      // ---- break point at tb from direction `who` (§5, Eqs. 5.2-5.6)
+      const double tb = __longlong_as_double(key);
+      b = sf::add_pos(b, sf::mul_pos(sf::u64_scaled(lam, F), sf::sub_pos(tb, tl)));
+      tl = tb;
+      const int pos = (int)__shfl_sync(kFull, npos, who);
+      int ux, uy, up_now;
+      if (who == 0) { hN ^= 1u << pos; up_now = (hN >> pos) & 1u; ux = pos; uy = 0; }
+      else if (who == 1) { hS ^= 1u << pos; up_now = (hS >> pos) & 1u; ux = pos; uy = H - 1; }
+      else if (who == 2) { hW ^= 1u << pos; up_now = (hW >> pos) & 1u; ux = 0; uy = pos; }
+      else { hE ^= 1u << pos; up_now = (hE >> pos) & 1u; ux = W - 1; uy = pos; }
+      refresh();
+      // class of the adjacent site after the change (owner lane uy), before it one less/more
+      const int cnew_l = 5 * (int)((row >> ux) & 1u) +
+                         (int)(((s0 >> ux) & 1u) + 2u * ((s1 >> ux) & 1u) + 4u * ((s2 >> ux) & 1u));
+      const int cnew = __shfl_sync(kFull, cnew_l, uy);
+      const int cold = cnew + (up_now ? -1 : 1);
+      myN = (unsigned)((int)myN + (lane == cnew) - (lane == cold));
+      lam = lam - p.P[cold] + p.P[cnew];
+      if (lane == who) {                     // advance the cursor
+        ++idx;
+        nt = nt2;
+        npos = npos2;
+        if (idx + 1 < len) {
+          const size_t a = (((size_t)rp * 4 + ein) * cap + idx + 1) * nr + qd;
+          nt2 = __ldcg(&p.ht[a]);
+          npos2 = __ldcg(&p.hp[a]);
+        } else {
+          nt2 = INF;
+        }
+      }
+      ++brk;
+    }
+    tau = tau_soft(tl, x, b, lam, F);
+  }
+
+  // ---- compare the new lists with the previous ones (§4 statement (c))
+  __syncwarp();
+  bool changed = overflow;
+  for (int e = 0; e < 4; ++e) {
+    if (!((e < 2) ? has_y : has_x)) continue;
+    const unsigned nn = (e == 0) ? olen0 : (e == 1) ? olen1 : (e == 2) ? olen2 : olen3;
+    const unsigned n_new = nn < (unsigned)cap ? nn : (unsigned)cap;
+    const unsigned n_old = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
+    bool diff = n_new != n_old;
+    const unsigned n_min = n_new < n_old ? n_new : n_old;
+    for (unsigned j = lane; j < n_min; j += 32) {
+      const size_t an = (((size_t)wp * 4 + e) * cap + j) * nr + r;
+      const size_t ao = (((size_t)rp * 4 + e) * cap + j) * nr + r;
+      if (__double_as_longlong(__ldcg(&p.ht[an])) != __double_as_longlong(__ldcg(&p.ht[ao])) ||
+          __ldcg(&p.hp[an]) != __ldcg(&p.hp[ao]))
+        diff = true;
+    }
+    changed |= __any_sync(kFull, diff);
+    if (lane == 0) p.hl[((size_t)wp * 4 + e) * nr + r] = n_new;
+  }
+  if (lane == 0) p.chg[(size_t)wp * nr + r] = changed ? 1 : 0;
+
+  // ---- tentative end state
+  const unsigned tc = cidx ^ 1u;
+  if (vlane) p.rows[((size_t)tc * H + lane) * nr + r] = row;
+  if (lane == 0) {
+    p.ci[tc * nr + r] = i;
+    p.cx[tc * nr + r] = x;
+    p.ckv[tc * nr + r] = kv;
+    p.cb[tc * nr + r] = b;
+    p.ct[tc * nr + r] = tl;
+    // window integrals: M0 span + 2 (t_end K - S), bonds likewise with 4
+    const double span = __dsub_rn(t_end, t_s);
+    Acc128 um = {0ull, 0}, ub = {0ull, 0};
+    const unsigned long long tend_fix = to_fixed(t_end, frac);
+    // t_end K - S as 128-bit: K t_end_fix is at most |K| 2^63
+    auto kt = [&](int k, Acc128& out, const Acc128& sum) {
+      const unsigned long long ak = (unsigned long long)(k < 0 ? -k : k);
+      const unsigned long long plo = ak * tend_fix, phi = __umul64hi(ak, tend_fix);
+      if (k >= 0) { out.lo = plo; out.hi = (long long)phi; }
+      else { out.lo = 0ull - plo; out.hi = -(long long)phi - (plo != 0ull ? 1 : 0); }
+      const unsigned long long n = out.lo - sum.lo;
+      out.hi = out.hi - sum.hi - (out.lo < sum.lo ? 1 : 0);
+      out.lo = n;
+    };
+    kt(ksig, um, ssig);
+    kt(kbeta, ub, sbeta);
+    const double im = __dadd_rn(__dmul_rn((double)mag0, span), __dmul_rn(2.0, um.value(frac)));
+    const double ib = __dadd_rn(__dmul_rn((double)bond0, span), __dmul_rn(4.0, ub.value(frac)));
+    p.cim[tc * nr + r] = __dadd_rn(__ldcg(&p.cim[cidx * nr + r]), im);
+    p.cib[tc * nr + r] = __dadd_rn(__ldcg(&p.cib[cidx * nr + r]), ib);
+    acc.events += events;
+    acc.breaks += brk;
+    if (bevents > acc.fmax) acc.fmax = bevents;
+    if ((unsigned)events > acc.emax) acc.emax = (unsigned)events;
+    acc.changed |= changed;
+    acc.overflow |= overflow;
+  }
+}
+
 // Halo words of region r from the committed rows of its four neighbours.
 __device__ void compute_halo(const KParams& p, int r, unsigned cidx) {
   const size_t nr = (size_t)p.NR;
@@ -592,18 +1084,28 @@ __device__ void fill_ring(const KParams& p, unsigned cidx) {
       p.rhi[r] = p.ci[cidx * nr + r] + (unsigned long long)p.K;
 }
 
-__global__ void __launch_bounds__(256) relax_kernel(KParams p) {
+// MODE 0: one lane per region (region lanes are the first rl threads of a
+// block); MODE 1: one warp per region (rl = warps per block).  Region slot j of
+// block b owns regions b*rl + j + k*(gridDim.x*rl).
+#ifndef SR_WARP_MIN_BLOCKS
+#define SR_WARP_MIN_BLOCKS 4
+#endif
+template <int MODE>
+__global__ void __launch_bounds__(MODE == 0 ? 256 : 128, MODE == 0 ? 1 : SR_WARP_MIN_BLOCKS)
+    relax_kernel(KParams p) {
   extern __shared__ uint32_t smem[];
   if ((int)blockIdx.x == p.skip_block) return;   // test hook: never reaches a barrier
-  // region lanes are the first rl threads of a block; lane j of block b owns
-  // regions b*rl + j + k*(gridDim.x*rl)
-  const int stride = p.rl;
-  const bool is_lane = (int)threadIdx.x < p.rl;
-  const int gthreads = gridDim.x * p.rl;
-  const int gtid = is_lane ? (int)(blockIdx.x * p.rl + threadIdx.x) : p.NR;
+  const int slot = MODE == 0 ? (int)threadIdx.x : (int)(threadIdx.x >> 5);
+  const bool is_slot = slot < p.rl;
+  const int sstride = gridDim.x * p.rl;
+  const int sfirst = is_slot ? (int)(blockIdx.x * p.rl + slot) : p.NR;
+  // plain per-thread striding for the simple phases
+  const int tfirst = MODE == 0 ? sfirst : (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int tstride = MODE == 0 ? sstride : (int)(gridDim.x * blockDim.x);
   Region g;
-  g.rows = smem + (is_lane ? threadIdx.x : 0);
-  g.N = smem + p.H * stride + (is_lane ? threadIdx.x : 0);
+  const int stride = p.rl;
+  g.rows = smem + (MODE == 0 && is_slot ? threadIdx.x : 0);
+  g.N = smem + p.H * stride + (MODE == 0 && is_slot ? threadIdx.x : 0);
   g.stride = stride;
   g.W = p.W;
   g.H = p.H;
@@ -615,11 +1117,26 @@ __global__ void __launch_bounds__(256) relax_kernel(KParams p) {
   unsigned cidx = *(volatile unsigned*)&st->cidx;
   unsigned giter = 0;
   double t_s = p.t0;
+  const bool reporter = MODE == 0 ? true : (threadIdx.x & 31) == 0;
+  unsigned long long run_cyc = 0ull;
+  // per-slot busy cycles, reported when the launch ends normally
+  struct Report {
+    DevStats* st;
+    const unsigned long long* cyc;
+    bool on;
+    __device__ ~Report() {
+      if (on) {
+        atomicAdd(&st->run_cycles, *cyc);
+        atomicMax(&st->run_cycles_max, *cyc);
+        atomicAdd(&st->slots, 1ull);
+      }
+    }
+  } report{st, &run_cyc, reporter && is_slot};
 
   for (int w = 0; w < p.nwin; ++w) {
     const double t_end = __dadd_rn(t_s, p.Tw);
     // canonical assumption (§5): no neighbour flips -> empty previous lists
-    for (int r = gtid; r < p.NR; r += gthreads)
+    for (int r = tfirst; r < p.NR; r += tstride)
       for (int e = 0; e < 4; ++e) p.hl[(size_t)e * nr + r] = 0u;   // parity 0
     fill_ring(p, cidx);
     if (!grid_barrier(st, p.timeout_cycles)) return;
@@ -627,22 +1144,31 @@ __global__ void __launch_bounds__(256) relax_kernel(KParams p) {
     int n = 1;
     bool converged = false;
     for (; n <= p.max_iters; ++n) {
-      const unsigned slot = giter % 3u;
+      const unsigned fslot = giter % 3u;
       ++giter;
       Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, false, false};
-      for (int r = gtid; r < p.NR; r += gthreads) run_region(p, r, n, cidx, t_s, t_end, g, acc);
-      if (acc.changed) atomicOr(&st->flags[slot], 1u);
-      if (acc.overflow) atomicOr(&st->status, ST_CAPACITY);
-      if (acc.events) atomicAdd(&st->generated, acc.events);
-      if (acc.breaks) atomicAdd(&st->breaks, acc.breaks);
-      if (acc.fmax) atomicMax(&st->max_f, acc.fmax);
-      if (acc.emax) atomicMax(&st->max_win_events, acc.emax);
-      if (acc.passes) atomicAdd(&st->region_passes, acc.passes);
-      if (acc.skips) atomicAdd(&st->region_skips, acc.skips);
+      const long long c0 = clock64();
+      for (int r = sfirst; r < p.NR; r += sstride) {
+        if (MODE == 0)
+          run_region(p, r, n, cidx, t_s, t_end, g, acc);
+        else
+          run_region_warp(p, r, n, cidx, t_s, t_end, acc);
+      }
+      run_cyc += (unsigned long long)(clock64() - c0);
+      if (reporter) {
+        if (acc.changed) atomicOr(&st->flags[fslot], 1u);
+        if (acc.overflow) atomicOr(&st->status, ST_CAPACITY);
+        if (acc.events) atomicAdd(&st->generated, acc.events);
+        if (acc.breaks) atomicAdd(&st->breaks, acc.breaks);
+        if (acc.fmax) atomicMax(&st->max_f, acc.fmax);
+        if (acc.emax) atomicMax(&st->max_win_events, acc.emax);
+        if (acc.passes) atomicAdd(&st->region_passes, acc.passes);
+        if (acc.skips) atomicAdd(&st->region_skips, acc.skips);
+      }
       if (!grid_barrier(st, p.timeout_cycles)) return;
-      if (blockIdx.x == 0 && threadIdx.x == 0) st->flags[(slot + 2u) % 3u] = 0u;
+      if (blockIdx.x == 0 && threadIdx.x == 0) st->flags[(fslot + 2u) % 3u] = 0u;
       if (*(volatile unsigned*)&st->status & ST_CAPACITY) return;   // window not committed
-      if (*(volatile unsigned*)&st->flags[slot] == 0u) {
+      if (*(volatile unsigned*)&st->flags[fslot] == 0u) {
         converged = true;
         break;
       }
@@ -653,8 +1179,8 @@ __global__ void __launch_bounds__(256) relax_kernel(KParams p) {
     }
     // ---- commit (statement 3 of §4: increment committed time by T_max)
     unsigned long long committed = 0;
-    for (int r = gtid; r < p.NR; r += gthreads)
-      committed += p.ci[(cidx ^ 1u) * nr + r] - p.ci[cidx * nr + r];
+    for (int r = tfirst; r < p.NR; r += tstride)
+      committed += __ldcg(&p.ci[(cidx ^ 1u) * nr + r]) - __ldcg(&p.ci[cidx * nr + r]);
     if (committed) atomicAdd(&st->committed, committed);
     cidx ^= 1u;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -667,7 +1193,7 @@ __global__ void __launch_bounds__(256) relax_kernel(KParams p) {
       st->windows_done = (unsigned)(w + 1);
     }
     if (!grid_barrier(st, p.timeout_cycles)) return;
-    for (int r = gtid; r < p.NR; r += gthreads) compute_halo(p, r, cidx);
+    for (int r = tfirst; r < p.NR; r += tstride) compute_halo(p, r, cidx);
     if (!grid_barrier(st, p.timeout_cycles)) return;
     t_s = t_end;
   }
@@ -804,6 +1330,22 @@ __global__ void eval_draws_kernel(uint32_t key0, uint32_t key1, uint32_t region,
   kv[j] = k;
 }
 
+__global__ void eval_softfloat_kernel(int op, const double* a, const double* b, double* out,
+                                      size_t n) {
+  const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double x = a[j], y = b[j];
+  double r;
+  switch (op) {
+    case 0: r = sf::add_pos(x, y); break;
+    case 1: r = sf::sub_pos(x, y); break;
+    case 2: r = sf::mul_pos(x, y); break;
+    case 3: r = sf::div_pos(x, y); break;
+    default: r = sf::u64_scaled((unsigned long long)__double_as_longlong(x), (int)y); break;
+  }
+  out[j] = r;
+}
+
 }  // namespace sr
 
 // ====================================================================== C ABI
@@ -835,7 +1377,7 @@ struct sr_ctx {
   double* h_obs_f;
   int8_t* stage;
   double t_c;
-  int rl, tpb, blocks;
+  int rl, tpb, blocks, mode;
   size_t smem;
   int last_nwin;
   unsigned long long launches;   // kernels launched by this context
@@ -959,8 +1501,9 @@ int launch_relax(sr_ctx* c, double t0, double Tw, int nwin) {
   k.nwin = nwin;
   if (cudaMemsetAsync(c->st, 0, offsetof(DevStats, cidx), c->stream) != cudaSuccess) return SR_ECUDA;
   void* args[] = {&k};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)relax_kernel, dim3(c->blocks),
-                                              dim3(c->tpb), args, c->smem, c->stream);
+  const void* fn = c->mode == 1 ? (const void*)relax_kernel<1> : (const void*)relax_kernel<0>;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->blocks), dim3(c->tpb), args, c->smem,
+                                              c->stream);
   if (e != cudaSuccess) return SR_ECUDA;
   c->launches += 1;
   if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
@@ -1076,6 +1619,32 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   // launch shape: spread the regions over every SM, one lane per region; a
   // block with few region lanes gets helper threads for the ring top-up
   const int H = p.region_h;
+  if (p.lanes_per_region != 0 && p.lanes_per_region != 1 && p.lanes_per_region != 32) {
+    std::free(c);
+    return SR_EINVAL;
+  }
+  // warp per region pays off while the regions fit the resident warps
+  c->mode = p.lanes_per_region == 32 ? 1 : (p.lanes_per_region == 1 ? 0 : -1);
+  if (c->mode == 1 || (c->mode == -1 && c->NR <= 24 * c->num_sms)) {
+    c->mode = 1;
+    int wpb = p.threads_per_block ? p.threads_per_block : 4;   // warps per block
+    if (wpb > 8) wpb = 8;
+    c->rl = wpb;
+    c->tpb = 32 * wpb;
+    c->smem = 0;
+    int per_sm_blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<1>, c->tpb, 0) !=
+            cudaSuccess ||
+        per_sm_blocks < 1) {
+      free_all(c);
+      std::free(c);
+      return SR_EUNSUPPORTED;
+    }
+    int blocks = p.blocks ? p.blocks : (c->NR + wpb - 1) / wpb;
+    if (blocks > per_sm_blocks * c->num_sms) blocks = per_sm_blocks * c->num_sms;
+    c->blocks = blocks;
+  } else {
+  c->mode = 0;
   int rl = p.threads_per_block;
   if (rl == 0) {
     const int per_sm = (c->NR + c->num_sms - 1) / c->num_sms;
@@ -1094,7 +1663,7 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   c->tpb = tpb;
   c->smem = (size_t)(H + 10) * rl * sizeof(uint32_t);
   int per_sm_blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel, tpb, c->smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0>, tpb, c->smem) !=
           cudaSuccess ||
       per_sm_blocks < 1) {
     free_all(c);
@@ -1106,6 +1675,7 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   const int max_res = per_sm_blocks * c->num_sms;
   if (blocks > max_res) blocks = max_res;
   c->blocks = blocks;
+  }
 
   const size_t nr = (size_t)c->NR;
   rc |= dalloc(&c->rows, 2 * (size_t)H * nr);
@@ -1246,6 +1816,11 @@ int sr_observables(sr_ctx* c, sr_obs* out) {
   out->max_f = h.max_f;
   out->capacity = (uint32_t)c->cap;
   out->launches = c->launches;
+  out->region_passes = h.region_passes;
+  out->region_skips = h.region_skips;
+  out->run_cycles = h.run_cycles;
+  out->run_cycles_max = h.run_cycles_max;
+  out->slots = h.slots;
   return SR_OK;
 }
 
@@ -1370,6 +1945,25 @@ int sr_eval_draws(uint64_t seed, uint32_t region, uint64_t i0, size_t n, double*
   if (rc == SR_OK && kV) rc = cuda_rc(cudaMemcpy(kV, dk, n * 8, cudaMemcpyDeviceToHost));
   cudaFree(dx);
   cudaFree(dk);
+  return rc;
+}
+
+int sr_eval_softfloat(int op, const double* a, const double* b, double* out, size_t n) {
+  if (op < 0 || op > 4 || !a || !b || !out) return SR_EINVAL;
+  if (n == 0) return SR_OK;
+  double *da = nullptr, *db = nullptr, *dout = nullptr;
+  int rc = SR_OK;
+  if (dalloc(&da, n) || dalloc(&db, n) || dalloc(&dout, n)) rc = SR_ENOMEM;
+  if (rc == SR_OK) rc = cuda_rc(cudaMemcpy(da, a, n * 8, cudaMemcpyHostToDevice));
+  if (rc == SR_OK) rc = cuda_rc(cudaMemcpy(db, b, n * 8, cudaMemcpyHostToDevice));
+  if (rc == SR_OK) {
+    eval_softfloat_kernel<<<(unsigned)((n + 255) / 256), 256>>>(op, da, db, dout, n);
+    rc = cuda_rc(cudaGetLastError());
+  }
+  if (rc == SR_OK) rc = cuda_rc(cudaMemcpy(out, dout, n * 8, cudaMemcpyDeviceToHost));
+  if (da) cudaFree(da);
+  if (db) cudaFree(db);
+  if (dout) cudaFree(dout);
   return rc;
 }
 
@@ -1522,7 +2116,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.tpb = tpb;
   c.smem = (size_t)(region_h + 10) * rl * sizeof(uint32_t);
   int per_sm_blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel, tpb, c.smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0>, tpb, c.smem) !=
           cudaSuccess ||
       per_sm_blocks < 1)
     return SR_EUNSUPPORTED;
@@ -1544,7 +2138,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   k.nwin = n_windows;
   if (cudaMemsetAsync(c.st, 0, offsetof(DevStats, cidx), c.stream) != cudaSuccess) return SR_ECUDA;
   void* args[] = {&k};
-  if (cudaLaunchCooperativeKernel((const void*)relax_kernel, dim3(c.blocks), dim3(c.tpb), args,
+  if (cudaLaunchCooperativeKernel((const void*)relax_kernel<0>, dim3(c.blocks), dim3(c.tpb), args,
                                   c.smem, c.stream) != cudaSuccess)
     return SR_ECUDA;
   DevStats hs;

@@ -17,11 +17,13 @@ pytestmark = pytest.mark.gpu
 sr = pytest.importorskip("paper_cs_0405053_gb300")
 
 
+@pytest.mark.parametrize("lpr", [1, 32])
 @pytest.mark.parametrize("Tw,per_call", [(0.25, 40), (1.0, 10), (4.0, 1)])
-def test_L1024_to_t100_bit_exact(Tw, per_call):
+def test_L1024_to_t100_bit_exact(Tw, per_call, lpr):
     L, W = 1024, 16
     trace = Tw == 1.0
-    lat = sr.Lattice(L, 1.0, 0.05, 1.0, (W, W), seed=1, trace_capacity=4096 if trace else 0)
+    lat = sr.Lattice(L, 1.0, 0.05, 1.0, (W, W), seed=1, trace_capacity=4096 if trace else 0,
+                     lanes_per_region=lpr)
     checkpoints, gpu = [], []
     t = 0.0
     n_total = int(round(100 / Tw))
@@ -61,7 +63,8 @@ def test_L1024_to_t100_bit_exact(Tw, per_call):
                                     (3.5, "up"), (3.5, "fair")])
 def test_L8192_short_interval_bit_exact(T, init):
     L, W = 8192, 32
-    lat = sr.Lattice(L, 1.0, 0.0, T, (W, W), seed=1, init=init)
+    lat = sr.Lattice(L, 1.0, 0.0, T, (W, W), seed=1, init=init,
+                     lanes_per_region=32 if T == 2.269 else 0)
     lat.run_windows(0.1, 2)
     mode = oracle.INIT_ALL_UP if init == "up" else oracle.INIT_FAIR_COIN
     ends = [0.1, 0.1 + 0.1]

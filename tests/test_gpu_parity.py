@@ -95,11 +95,15 @@ def test_rate_table_matches():
 
 
 # ----------------------------------------------------------------- trajectories
+LPR = [1, 32]     # one lane per region, one warp per region
+
+
+@pytest.mark.parametrize("lpr", LPR)
 @pytest.mark.parametrize("L,W,H", [(3, 1, 1), (4, 2, 2), (8, 4, 4), (8, 8, 8), (6, 3, 2), (12, 4, 3),
                                    (16, 16, 4), (16, 4, 16), (16, 1, 16), (9, 3, 1), (32, 8, 8),
                                    (30, 10, 6), (32, 32, 32), (64, 32, 32)])
-def test_small_lattices_bit_exact(L, W, H):
-    _compare(L, W, H, seed=L * 31 + W, T=1.7, Tw=0.7, nwin=4)
+def test_small_lattices_bit_exact(L, W, H, lpr):
+    _compare(L, W, H, seed=L * 31 + W, T=1.7, Tw=0.7, nwin=4, lanes_per_region=lpr)
 
 
 @pytest.mark.parametrize("T,h,J,rates,init", [(1.0, 0.0, 1.0, "metropolis", "fair"),
@@ -109,8 +113,10 @@ def test_small_lattices_bit_exact(L, W, H):
                                               (1e300, 0.0, 1.0, "metropolis", "fair"),
                                               (2.0, 0.3, 0.0, "metropolis", "fair"),
                                               (0.005, 0.05, 1.0, "metropolis", "fair")])
-def test_parameters_bit_exact(T, h, J, rates, init):
-    _compare(24, 8, 6, J=J, h=h, T=T, rates=rates, init=init, seed=5, Tw=0.5, nwin=4)
+@pytest.mark.parametrize("lpr", LPR)
+def test_parameters_bit_exact(T, h, J, rates, init, lpr):
+    _compare(24, 8, 6, J=J, h=h, T=T, rates=rates, init=init, seed=5, Tw=0.5, nwin=4,
+             lanes_per_region=lpr)
 
 
 def test_given_initial_spins():
@@ -119,11 +125,12 @@ def test_given_initial_spins():
     _compare(16, 4, 4, given=given, seed=9, nwin=3)
 
 
+@pytest.mark.parametrize("lpr", LPR)
 @pytest.mark.parametrize("seed", range(1, 9))
-def test_small_config_L64_bit_exact(seed):
+def test_small_config_L64_bit_exact(seed, lpr):
     """L = 64, 4 x 4 regions of 16 x 16, J = 1, h = 0.05, T = 1.5, fair coin,
     window 1.0, run to t = 10."""
-    _compare(64, 16, 16, h=0.05, T=1.5, seed=seed, Tw=1.0, nwin=10)
+    _compare(64, 16, 16, h=0.05, T=1.5, seed=seed, Tw=1.0, nwin=10, lanes_per_region=lpr)
 
 
 def test_window_length_does_not_change_the_trajectory():
@@ -173,8 +180,14 @@ def test_iterations_follow_the_canonical_assumption():
         assert (g[w] == 1) == (nb == 0), (w, g[w], nb)
 
 
-def test_medium_lattice_bit_exact():
-    _compare(256, 16, 16, h=0.05, T=1.0, seed=1, Tw=1.0, nwin=3, trace=False)
+@pytest.mark.parametrize("lpr", LPR)
+def test_medium_lattice_bit_exact(lpr):
+    _compare(256, 16, 16, h=0.05, T=1.0, seed=1, Tw=1.0, nwin=3, trace=False, lanes_per_region=lpr)
+
+
+@pytest.mark.parametrize("lpr", LPR)
+def test_capacity_growth_exact_both_mappings(lpr):
+    _compare(64, 16, 16, T=3.5, seed=6, Tw=2.0, nwin=2, lanes_per_region=lpr)
 
 
 # ----------------------------------------------------------------- failure paths
