@@ -145,7 +145,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     seed = 1 + rank
     stream = torch.cuda.current_stream()
-    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr)
+    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr,
+                     lanes_per_warp=args.lpw, time_arith=args.arith)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def one_pass(record):
@@ -212,7 +213,8 @@ def run_ours(args):
     rng = np.random.default_rng(1000 + rank)
     init_host = torch.from_numpy(np.where(rng.random((L, L)) < 0.5, 1, -1).astype(np.int8)).pin_memory()
     out_host = torch.empty((L, L), dtype=torch.int8).pin_memory()
-    e2e_lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr)
+    e2e_lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr,
+                         lanes_per_warp=args.lpw, time_arith=args.arith)
     e2e_committed, e2e_time = 0, 0.0
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -293,7 +295,8 @@ def run_profile_case(args):
 
     import paper_cs_0405053_gb300 as sr
     torch.cuda.set_device(0)
-    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=1, lanes_per_region=args.lpr)
+    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=1, lanes_per_region=args.lpr,
+                     lanes_per_warp=args.lpw, time_arith=args.arith)
     t0 = None
     for _ in range(args.warmup):
         lat.reset()
@@ -307,7 +310,8 @@ def run_profile_case(args):
     o = lat.observables()
     mhz = 2070.0
     print(json.dumps({"profile_case": True, "tw": args.tw, "windows": args.windows,
-                      "lanes_per_region": args.lpr, "ms": dt * 1e3,
+                      "lanes_per_region": args.lpr, "lanes_per_warp": args.lpw, "arith": args.arith,
+                      "blocks": lat.blocks, "ms": dt * 1e3,
                       "committed": o.committed, "generated": o.generated,
                       "iterations": o.iterations, "passes": o.region_passes,
                       "skips": o.region_skips,
@@ -328,6 +332,8 @@ def main():
     ap.add_argument("--windows", type=int, default=5)
     ap.add_argument("--lpr", type=int, default=0,
                     help="lanes per region: 1, 32 or 0 (automatic)")
+    ap.add_argument("--lpw", type=int, default=0, help="region lanes per warp (lane mapping)")
+    ap.add_argument("--arith", type=int, default=0, help="time arithmetic: 1 FP64, 2 integer")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

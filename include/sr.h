@@ -68,8 +68,12 @@ typedef struct sr_params {
                                    (grows by doubling when exceeded, see sr_run_windows) */
   int max_iters;                /* iteration cap per window; 0 = 1<<16 */
   int trace_capacity;           /* committed events recorded per region; 0 = no trace */
-  int lanes_per_region;         /* 1 = one lane per region, 32 = one warp per region,
-                                   0 = automatic (a warp while the regions fit the resident warps) */
+  int lanes_per_region;         /* 32 = one warp per region; 1 or 0 = one lane per region */
+  int lanes_per_warp;           /* with one lane per region: region lanes in each warp (1..32);
+                                   fewer lanes give more warps and less divergence; 0 = automatic */
+  int time_arith;               /* waiting-time arithmetic with one lane per region: 1 = FP64
+                                   instructions, 2 = integer-emulated doubles (identical bits),
+                                   0 = automatic */
   int threads_per_block;        /* region slots per block (lanes, or warps with a warp per
                                    region); 0 = automatic */
   int block_threads;            /* threads per block, >= region lanes; the extra threads help

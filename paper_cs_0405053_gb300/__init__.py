@@ -37,7 +37,8 @@ class _Params(C.Structure):
                 ("region_w", C.c_int), ("region_h", C.c_int), ("seed", C.c_uint64),
                 ("init_mode", C.c_int), ("rates", C.c_int), ("capacity", C.c_int),
                 ("max_iters", C.c_int), ("trace_capacity", C.c_int),
-                ("lanes_per_region", C.c_int), ("threads_per_block", C.c_int), ("block_threads", C.c_int), ("blocks", C.c_int),
+                ("lanes_per_region", C.c_int), ("lanes_per_warp", C.c_int), ("time_arith", C.c_int),
+                ("threads_per_block", C.c_int), ("block_threads", C.c_int), ("blocks", C.c_int),
                 ("barrier_timeout_ms", C.c_int), ("test_barrier_skip_block", C.c_int),
                 ("stream", C.c_void_p)]
 
@@ -164,7 +165,8 @@ class Lattice:
     def __init__(self, L: int, J: float = 1.0, h: float = 0.0, T: float = 1.0,
                  region: Tuple[int, int] = (16, 16), seed: int = 1, init: str = "fair",
                  rates: str = "metropolis", capacity: int = 0, max_iters: int = 0,
-                 trace_capacity: int = 0, lanes_per_region: int = 0, threads_per_block: int = 0,
+                 trace_capacity: int = 0, lanes_per_region: int = 0, lanes_per_warp: int = 0,
+                 time_arith: int = 0, threads_per_block: int = 0,
                  block_threads: int = 0,
                  blocks: int = 0,
                  barrier_timeout_ms: int = 0, test_barrier_skip_block: int = -1,
@@ -177,7 +179,8 @@ class Lattice:
         self.seed = seed
         self.trace_capacity = trace_capacity
         prm = _Params(L, J, h, T, region[0], region[1], seed, INIT_MODES[init], RATES[rates],
-                      capacity, max_iters, trace_capacity, lanes_per_region, threads_per_block,
+                      capacity, max_iters, trace_capacity, lanes_per_region, lanes_per_warp,
+                      time_arith, threads_per_block,
                       block_threads, blocks,
                       barrier_timeout_ms, test_barrier_skip_block, stream)
         self._ctx = _P()

@@ -60,7 +60,9 @@ struct KParams {
   int L, W, H, NX, NY, NR;
   int spans_x, spans_y;
   unsigned long long P[10];
+  unsigned long long Rp[10];    // floor((2^64 - 1) / P[k]) (0 when P[k] = 0)
   double scale;                 // 2^-F
+  int F;
   uint32_t key0, key1;
   uint32_t* rows;               // [2][H][NR]   spin rows, bit x = site x of the row
   uint32_t* halo;               // [4][NR]      N, S, W, E halo words at t_c
@@ -83,7 +85,8 @@ struct KParams {
   unsigned long long* rkv;      // [K][NR]      presimulated V bits
   unsigned long long* rhi;      // [NR]         ring holds events [committed index, rhi)
   int K;                        // ring length (power of two)
-  int rl;                       // region lanes per block (the other threads only help fill)
+  int rl;                       // region slots per block (the other threads only help fill)
+  int lanes;                    // lane mappings: region lanes in each warp
   DevStats* st;
   uint32_t* win_iters;          // [kWinRing]
   double t0, Tw;
@@ -206,6 +209,81 @@ __device__ __forceinline__ void move_class(const Region& g, const KParams& p, in
   lam = lam - p.P[from] + p.P[to];
 }
 
+// tau of Eq. 3.4 / 5.6 in integer-emulated doubles (same bits as tau_hat).
+__device__ __forceinline__ double tau_soft(double t_last, double x, double b, unsigned long long lam,
+                                           int F) {
+  if (lam == 0ull) return __longlong_as_double(0x7FF0000000000000ll);
+  double d = sf::sub_pos(x, b);
+  if (__double_as_longlong(d) < 0ll) d = 0.0;      // sign bit: the remaining hazard is used up
+  const double t = sf::add_pos(t_last, sf::div_pos(d, sf::u64_scaled(lam, F)));
+  if (__double_as_longlong(t) <= __double_as_longlong(t_last))
+    return __longlong_as_double(__double_as_longlong(t_last) + 1ll);
+  return t;
+}
+
+// 128-bit signed accumulator of fixed-point times (observables).
+struct Acc128 {
+  unsigned long long lo;
+  long long hi;
+  __device__ __forceinline__ void add(long long k, unsigned long long v) {   // += k * v, |k| <= 2
+    unsigned long long a = v;
+    if (k == 2 || k == -2) a = v << 1;
+    const long long ahi = (k == 2 || k == -2) ? (long long)(v >> 63) : 0;
+    if (k > 0) {
+      const unsigned long long n = lo + a;
+      hi += ahi + (n < lo ? 1 : 0);
+      lo = n;
+    } else if (k < 0) {
+      const unsigned long long n = lo - a;
+      hi -= ahi + (lo < a ? 1 : 0);
+      lo = n;
+    }
+  }
+  __device__ __forceinline__ double value(int frac) const {   // as a double times 2^-frac
+    return __dadd_rn(__dmul_rn((double)hi, __longlong_as_double((long long)(1023 + 64 - frac) << 52)),
+                     __dmul_rn(__ull2double_rn(lo), __longlong_as_double((long long)(1023 - frac) << 52)));
+  }
+};
+
+// t >= 0 as an integer multiple of 2^-frac (truncated), t * 2^frac < 2^63.
+__device__ __forceinline__ unsigned long long to_fixed(double t, int frac) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  if (b == 0ull) return 0ull;
+  const int e = (int)(b >> 52) - 1075 + frac;       // t = m 2^(ebits - 1075)
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  if (e >= 0) return m << e;
+  if (e <= -64) return 0ull;
+  return m >> (-e);
+}
+
+// K t_end - S as a 128-bit fixed-point number (the window term of a time integral).
+__device__ __forceinline__ Acc128 window_moment(int k, double t_end, int frac, const Acc128& sum) {
+  Acc128 out;
+  const unsigned long long tend_fix = to_fixed(t_end, frac);
+  const unsigned long long ak = (unsigned long long)(k < 0 ? -k : k);
+  const unsigned long long plo = ak * tend_fix, phi = __umul64hi(ak, tend_fix);
+  if (k >= 0) {
+    out.lo = plo;
+    out.hi = (long long)phi;
+  } else {
+    out.lo = 0ull - plo;
+    out.hi = -(long long)phi - (plo != 0ull ? 1 : 0);
+  }
+  const unsigned long long n = out.lo - sum.lo;
+  out.hi = out.hi - sum.hi - (out.lo < sum.lo ? 1 : 0);
+  out.lo = n;
+  return out;
+}
+
+// floor(D / P_k) for the position within class k (Eqs. 3.7-3.8): a multiply by
+// the reciprocal floor((2^64-1)/P_k) undershoots by at most one.
+__device__ __forceinline__ unsigned long long class_pos(unsigned long long D, unsigned long long Pk,
+                                                        unsigned long long Rk) {
+  unsigned long long j = __umul64hi(D, Rk);
+  if ((j + 1ull) * Pk <= D) ++j;
+  return j;
+}
+
 // ---------------------------------------------------------------- region pass
 struct Acc {
   unsigned long long events, breaks, passes, skips;
@@ -218,6 +296,21 @@ struct Acc {
 // merges the neighbours' previous-iteration boundary lists as break points,
 // writes the tentative end state to copy cidx ^ 1 and its own boundary lists to
 // parity wp, comparing them with its lists of the previous iteration.
+// SOFT = 1: the waiting-time chain in integer-emulated doubles; 0: FP64
+// instructions.  Both round every operation once (IEEE), so the bits agree.
+template <int SOFT>
+__device__ __forceinline__ double tau_any(double t_last, double x, double b, unsigned long long lam,
+                                          const KParams& p) {
+  return SOFT ? tau_soft(t_last, x, b, lam, p.F) : tau_hat(t_last, x, b, lam, p.scale);
+}
+template <int SOFT>
+__device__ __forceinline__ double accrue_any(double b, double tb, double tl, unsigned long long lam,
+                                             const KParams& p) {
+  return SOFT ? sf::add_pos(b, sf::mul_pos(sf::u64_scaled(lam, p.F), sf::sub_pos(tb, tl)))
+              : accrue(b, tb, tl, lam, p.scale);
+}
+
+template <int SOFT>
 __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, double t_s,
                            double t_end, Region& g, Acc& acc) {
   const int W = p.W, H = p.H, NR = p.NR;
@@ -346,21 +439,29 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
   unsigned long long events = 0, brk = 0;
   unsigned bevents = 0;
   int ksig = 0, kbeta = 0;
-  double ssig = 0.0, sbeta = 0.0;
+  // window integrals of the observables in fixed point (times as multiples of 2^-frac)
+  const int frac = 62 - (int)((((unsigned long long)__double_as_longlong(t_end)) >> 52) - 1022);
+  Acc128 ssig = {0ull, 0}, sbeta = {0ull, 0};
   const uint32_t gx0 = (uint32_t)(rx * W), gy0 = (uint32_t)(ry * H);
+  const long long tend_b = __double_as_longlong(t_end);
 
-  double tau = tau_hat(tl, x, b, lam, p.scale);
+  // times are >= 0, so their bit patterns order like their values
+  double tau = tau_any<SOFT>(tl, x, b, lam, p);
   for (;;) {
     // earliest pending break point (ties: any order, a zero-length segment adds +0)
-    double tb = nt[0];
+    long long tbb = __double_as_longlong(nt[0]);
     int db = 0;
 #pragma unroll
-    for (int d = 1; d < 4; ++d)
-      if (nt[d] < tb) { tb = nt[d]; db = d; }
+    for (int d = 1; d < 4; ++d) {
+      const long long v = __double_as_longlong(nt[d]);
+      if (v < tbb) { tbb = v; db = d; }
+    }
+    const double tb = __longlong_as_double(tbb);
+    const long long taub = __double_as_longlong(tau);
 
-    if (tau <= tb) {
+    if (taub <= tbb) {
       // ---- own event at tau, unless it falls past the window (§5: tau_m < t_c + T_max)
-      if (!(tau < t_end)) break;
+      if (!(taub < tend_b)) break;
       // class k* of Eqs. 3.5-3.6, exactly: P = V*Lambda*2^(53+F) as a 128-bit
       // integer (q53, rem); class k is chosen when P <= A(k) * 2^53.
       const unsigned long long mV = 2ull * kv + 1ull;
@@ -376,7 +477,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       }
       // position within the class, Eqs. 3.7-3.8: floor((V*Lambda - A(k*-1)) / p_k*)
       const unsigned Nks = g.N[ks * g.stride];
-      unsigned long long j = (q53 - Aprev) / p.P[ks];
+      unsigned long long j = class_pos(q53 - Aprev, p.P[ks], p.Rp[ks]);
       if (j >= Nks) j = Nks - 1;
       unsigned jj = (unsigned)j;
       // the jj-th class-k* site in row-major order (linear order of §3, Phase 3)
@@ -415,12 +516,12 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       // observables: dM = 2 sig, dBonds = 4 beta (Eq. 2.1 book-keeping)
       const int sig = s_old ? -1 : 1;
       const int beta = sig * (nup - 2);
-      ksig += sig;
-      ssig = (sig > 0) ? __dadd_rn(ssig, tau) : __dsub_rn(ssig, tau);
-      if (beta != 0) {
+      {
+        const unsigned long long tfix = to_fixed(tau, frac);
+        ksig += sig;
+        ssig.add(sig, tfix);
         kbeta += beta;
-        const double bt = (beta == 2 || beta == -2) ? __dadd_rn(tau, tau) : tau;
-        sbeta = (beta > 0) ? __dadd_rn(sbeta, bt) : __dsub_rn(sbeta, bt);
+        sbeta.add(beta, tfix);
       }
 
       // ---- boundary history (§5: the single layer of border atoms)
@@ -479,7 +580,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       }
     } else {
       // ---- break point: a neighbour flip at tb < tau (§5, Eqs. 5.2-5.6)
-      b = accrue(b, tb, tl, lam, p.scale);
+      b = accrue_any<SOFT>(b, tb, tl, lam, p);
       tl = tb;
       const unsigned pos = npos[db];
       int ux, uy, up_now;
@@ -503,7 +604,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       }
       ++brk;
     }
-    tau = tau_hat(tl, x, b, lam, p.scale);
+    tau = tau_any<SOFT>(tl, x, b, lam, p);
   }
 
 #pragma unroll
@@ -523,13 +624,15 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
   p.ckv[tc * nr + r] = kv;
   p.cb[tc * nr + r] = b;
   p.ct[tc * nr + r] = tl;
-  const double span = __dsub_rn(t_end, t_s);
-  const double im = __dadd_rn(__dmul_rn((double)mag0, span),
-                              __dmul_rn(2.0, __dsub_rn(__dmul_rn(t_end, (double)ksig), ssig)));
-  const double ib = __dadd_rn(__dmul_rn((double)bond0, span),
-                              __dmul_rn(4.0, __dsub_rn(__dmul_rn(t_end, (double)kbeta), sbeta)));
-  p.cim[tc * nr + r] = __dadd_rn(p.cim[cidx * nr + r], im);
-  p.cib[tc * nr + r] = __dadd_rn(p.cib[cidx * nr + r], ib);
+  {
+    const double span = __dsub_rn(t_end, t_s);
+    const Acc128 um = window_moment(ksig, t_end, frac, ssig);
+    const Acc128 ub = window_moment(kbeta, t_end, frac, sbeta);
+    const double im = __dadd_rn(__dmul_rn((double)mag0, span), __dmul_rn(2.0, um.value(frac)));
+    const double ib = __dadd_rn(__dmul_rn((double)bond0, span), __dmul_rn(4.0, ub.value(frac)));
+    p.cim[tc * nr + r] = __dadd_rn(p.cim[cidx * nr + r], im);
+    p.cib[tc * nr + r] = __dadd_rn(p.cib[cidx * nr + r], ib);
+  }
 
   acc.events += events;
   acc.breaks += brk;
@@ -564,53 +667,6 @@ __device__ __forceinline__ long long shfl_xor_s64(long long v, int m) {
   const unsigned lo = __shfl_xor_sync(kFull, (unsigned)v, m);
   const unsigned hi = __shfl_xor_sync(kFull, (unsigned)((unsigned long long)v >> 32), m);
   return (long long)(((unsigned long long)hi << 32) | lo);
-}
-
-// tau of Eq. 3.4 / 5.6 in integer-emulated doubles (same bits as tau_hat).
-__device__ __forceinline__ double tau_soft(double t_last, double x, double b, unsigned long long lam,
-                                           int F) {
-  if (lam == 0ull) return __longlong_as_double(0x7FF0000000000000ll);
-  double d = sf::sub_pos(x, b);
-  if (d < 0.0) d = 0.0;
-  const double t = sf::add_pos(t_last, sf::div_pos(d, sf::u64_scaled(lam, F)));
-  if (__double_as_longlong(t) <= __double_as_longlong(t_last))
-    return __longlong_as_double(__double_as_longlong(t_last) + 1ll);
-  return t;
-}
-
-// 128-bit signed accumulator of fixed-point times (observables).
-struct Acc128 {
-  unsigned long long lo;
-  long long hi;
-  __device__ __forceinline__ void add(long long k, unsigned long long v) {   // += k * v, |k| <= 2
-    unsigned long long a = v;
-    if (k == 2 || k == -2) a = v << 1;
-    const long long ahi = (k == 2 || k == -2) ? (long long)(v >> 63) : 0;
-    if (k > 0) {
-      const unsigned long long n = lo + a;
-      hi += ahi + (n < lo ? 1 : 0);
-      lo = n;
-    } else if (k < 0) {
-      const unsigned long long n = lo - a;
-      hi -= ahi + (lo < a ? 1 : 0);
-      lo = n;
-    }
-  }
-  __device__ __forceinline__ double value(int frac) const {   // as a double times 2^-frac
-    return __dadd_rn(__dmul_rn((double)hi, __longlong_as_double((long long)(1023 + 64 - frac) << 52)),
-                     __dmul_rn(__ull2double_rn(lo), __longlong_as_double((long long)(1023 - frac) << 52)));
-  }
-};
-
-// t >= 0 as an integer multiple of 2^-frac (truncated), t * 2^frac < 2^63.
-__device__ __forceinline__ unsigned long long to_fixed(double t, int frac) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
-  if (b == 0ull) return 0ull;
-  const int e = (int)(b >> 52) - 1075 + frac;       // t = m 2^(ebits - 1075)
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  if (e >= 0) return m << e;
-  if (e <= -64) return 0ull;
-  return m >> (-e);
 }
 
 __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned cidx, double t_s,
@@ -678,11 +734,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
     px = __ldcg(&p.rx[a]);
     pkv = __ldcg(&p.rkv[a]);
   }
-  int F = 0;
-  {
-    unsigned long long sc = (unsigned long long)__double_as_longlong(p.scale);
-    F = 1023 - (int)(sc >> 52);
-  }
+  const int F = p.F;
 
   // neighbour words and per-position up counts of my row
   uint32_t s0, s1, s2;
@@ -786,15 +838,9 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
       const unsigned Nks = __shfl_sync(kFull, myN, ks);
       const unsigned long long Pk = p.P[ks];
       // position in the class (Eqs. 3.7-3.8): floor((V Lambda - A(k*-1)) / p_k*)
-      const unsigned long long D = q53 - Aprev;
-      unsigned j = (unsigned)__float2uint_rz(__fdividef(__ull2float_rn(D), __ull2float_rn(Pk)));
-      if (j > Nks) j = Nks;
-#pragma unroll
-      for (int fix = 0; fix < 2; ++fix) {
-        if ((unsigned long long)j * Pk > D) --j;
-        else if ((unsigned long long)(j + 1) * Pk <= D) ++j;
-      }
-      if (j >= Nks) j = Nks - 1;
+      unsigned long long jl = class_pos(q53 - Aprev, Pk, p.Rp[ks]);
+      if (jl >= Nks) jl = Nks - 1;
+      const unsigned j = (unsigned)jl;
       // the j-th class-k* site in row-major order
       const int sp = ks >= 5;
       const int nn = ks - 5 * sp;
@@ -1001,20 +1047,8 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
     p.ct[tc * nr + r] = tl;
     // window integrals: M0 span + 2 (t_end K - S), bonds likewise with 4
     const double span = __dsub_rn(t_end, t_s);
-    Acc128 um = {0ull, 0}, ub = {0ull, 0};
-    const unsigned long long tend_fix = to_fixed(t_end, frac);
-    // t_end K - S as 128-bit: K t_end_fix is at most |K| 2^63
-    auto kt = [&](int k, Acc128& out, const Acc128& sum) {
-      const unsigned long long ak = (unsigned long long)(k < 0 ? -k : k);
-      const unsigned long long plo = ak * tend_fix, phi = __umul64hi(ak, tend_fix);
-      if (k >= 0) { out.lo = plo; out.hi = (long long)phi; }
-      else { out.lo = 0ull - plo; out.hi = -(long long)phi - (plo != 0ull ? 1 : 0); }
-      const unsigned long long n = out.lo - sum.lo;
-      out.hi = out.hi - sum.hi - (out.lo < sum.lo ? 1 : 0);
-      out.lo = n;
-    };
-    kt(ksig, um, ssig);
-    kt(kbeta, ub, sbeta);
+    const Acc128 um = window_moment(ksig, t_end, frac, ssig);
+    const Acc128 ub = window_moment(kbeta, t_end, frac, sbeta);
     const double im = __dadd_rn(__dmul_rn((double)mag0, span), __dmul_rn(2.0, um.value(frac)));
     const double ib = __dadd_rn(__dmul_rn((double)bond0, span), __dmul_rn(4.0, ub.value(frac)));
     p.cim[tc * nr + r] = __dadd_rn(__ldcg(&p.cim[cidx * nr + r]), im);
@@ -1079,8 +1113,8 @@ __device__ void fill_ring(const KParams& p, unsigned cidx) {
     }
   }
   __syncthreads();
-  if ((int)threadIdx.x < p.rl)
-    for (int r = blockIdx.x * p.rl + threadIdx.x; r < p.NR; r += lstride)
+  for (int l = threadIdx.x; l < p.rl; l += blockDim.x)
+    for (int r = blockIdx.x * p.rl + l; r < p.NR; r += lstride)
       p.rhi[r] = p.ci[cidx * nr + r] + (unsigned long long)p.K;
 }
 
@@ -1088,24 +1122,30 @@ __device__ void fill_ring(const KParams& p, unsigned cidx) {
 // block); MODE 1: one warp per region (rl = warps per block).  Region slot j of
 // block b owns regions b*rl + j + k*(gridDim.x*rl).
 #ifndef SR_WARP_MIN_BLOCKS
-#define SR_WARP_MIN_BLOCKS 4
+#define SR_WARP_MIN_BLOCKS 7
 #endif
+// MODE 0 / 2: one lane per region with FP64 / integer-emulated time
+// arithmetic; the first `lanes` lanes of every warp are region lanes.  MODE 1:
+// one warp per region.  Region slot j of block b owns regions
+// b*rl + j + k*(gridDim.x*rl).
 template <int MODE>
-__global__ void __launch_bounds__(MODE == 0 ? 256 : 128, MODE == 0 ? 1 : SR_WARP_MIN_BLOCKS)
+__global__ void __launch_bounds__(MODE == 1 ? 128 : 256, MODE == 1 ? SR_WARP_MIN_BLOCKS : 1)
     relax_kernel(KParams p) {
   extern __shared__ uint32_t smem[];
   if ((int)blockIdx.x == p.skip_block) return;   // test hook: never reaches a barrier
-  const int slot = MODE == 0 ? (int)threadIdx.x : (int)(threadIdx.x >> 5);
-  const bool is_slot = slot < p.rl;
+  constexpr bool LANES = MODE != 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = LANES ? warp * p.lanes + lane : warp;
+  const bool is_slot = (LANES ? lane < p.lanes : true) && slot < p.rl;
   const int sstride = gridDim.x * p.rl;
   const int sfirst = is_slot ? (int)(blockIdx.x * p.rl + slot) : p.NR;
   // plain per-thread striding for the simple phases
-  const int tfirst = MODE == 0 ? sfirst : (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int tstride = MODE == 0 ? sstride : (int)(gridDim.x * blockDim.x);
+  const int tfirst = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int tstride = (int)(gridDim.x * blockDim.x);
   Region g;
   const int stride = p.rl;
-  g.rows = smem + (MODE == 0 && is_slot ? threadIdx.x : 0);
-  g.N = smem + p.H * stride + (MODE == 0 && is_slot ? threadIdx.x : 0);
+  g.rows = smem + (LANES && is_slot ? slot : 0);
+  g.N = smem + p.H * stride + (LANES && is_slot ? slot : 0);
   g.stride = stride;
   g.W = p.W;
   g.H = p.H;
@@ -1117,7 +1157,7 @@ __global__ void __launch_bounds__(MODE == 0 ? 256 : 128, MODE == 0 ? 1 : SR_WARP
   unsigned cidx = *(volatile unsigned*)&st->cidx;
   unsigned giter = 0;
   double t_s = p.t0;
-  const bool reporter = MODE == 0 ? true : (threadIdx.x & 31) == 0;
+  const bool reporter = LANES ? true : (threadIdx.x & 31) == 0;
   unsigned long long run_cyc = 0ull;
   // per-slot busy cycles, reported when the launch ends normally
   struct Report {
@@ -1150,7 +1190,9 @@ __global__ void __launch_bounds__(MODE == 0 ? 256 : 128, MODE == 0 ? 1 : SR_WARP
       const long long c0 = clock64();
       for (int r = sfirst; r < p.NR; r += sstride) {
         if (MODE == 0)
-          run_region(p, r, n, cidx, t_s, t_end, g, acc);
+          run_region<0>(p, r, n, cidx, t_s, t_end, g, acc);
+        else if (MODE == 2)
+          run_region<1>(p, r, n, cidx, t_s, t_end, g, acc);
         else
           run_region_warp(p, r, n, cidx, t_s, t_end, acc);
       }
@@ -1377,7 +1419,7 @@ struct sr_ctx {
   double* h_obs_f;
   int8_t* stage;
   double t_c;
-  int rl, tpb, blocks, mode;
+  int rl, tpb, blocks, mode, lanes;
   size_t smem;
   int last_nwin;
   unsigned long long launches;   // kernels launched by this context
@@ -1422,8 +1464,12 @@ KParams make_params(const sr_ctx* c) {
   k.NR = c->NR;
   k.spans_x = c->NX == 1;
   k.spans_y = c->NY == 1;
-  for (int i = 0; i < 10; ++i) k.P[i] = c->P[i];
+  for (int i = 0; i < 10; ++i) {
+    k.P[i] = c->P[i];
+    k.Rp[i] = c->P[i] ? ~0ull / c->P[i] : 0ull;
+  }
   k.scale = c->scale;
+  k.F = c->F;
   k.key0 = (uint32_t)c->prm.seed;
   k.key1 = (uint32_t)(c->prm.seed >> 32);
   k.rows = c->rows;
@@ -1448,6 +1494,7 @@ KParams make_params(const sr_ctx* c) {
   k.rhi = c->rhi;
   k.K = c->K;
   k.rl = c->rl;
+  k.lanes = c->lanes;
   k.st = c->st;
   k.win_iters = c->win_iters;
   k.max_iters = c->prm.max_iters;
@@ -1501,10 +1548,14 @@ int launch_relax(sr_ctx* c, double t0, double Tw, int nwin) {
   k.nwin = nwin;
   if (cudaMemsetAsync(c->st, 0, offsetof(DevStats, cidx), c->stream) != cudaSuccess) return SR_ECUDA;
   void* args[] = {&k};
-  const void* fn = c->mode == 1 ? (const void*)relax_kernel<1> : (const void*)relax_kernel<0>;
+  const void* fn = c->mode == 1 ? (const void*)relax_kernel<1>
+                                : (c->mode == 2 ? (const void*)relax_kernel<2> : (const void*)relax_kernel<0>);
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->blocks), dim3(c->tpb), args, c->smem,
                                               c->stream);
-  if (e != cudaSuccess) return SR_ECUDA;
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // a refused launch leaves no error behind for later calls
+    return SR_ECUDA;
+  }
   c->launches += 1;
   if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
       cudaSuccess)
@@ -1616,65 +1667,70 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
     c->own_stream = true;
   }
 
-  // launch shape: spread the regions over every SM, one lane per region; a
-  // block with few region lanes gets helper threads for the ring top-up
+  // launch shape.  Warp per region while the regions fit the resident warps;
+  // otherwise one lane per region, with few region lanes per warp when the
+  // regions are few (less divergence, more warps to hide latency) and FP64
+  // time arithmetic while the FP64 pipe is not the limit.
   const int H = p.region_h;
   if (p.lanes_per_region != 0 && p.lanes_per_region != 1 && p.lanes_per_region != 32) {
     std::free(c);
     return SR_EINVAL;
   }
-  // warp per region pays off while the regions fit the resident warps
-  c->mode = p.lanes_per_region == 32 ? 1 : (p.lanes_per_region == 1 ? 0 : -1);
-  if (c->mode == 1 || (c->mode == -1 && c->NR <= 24 * c->num_sms)) {
+  if (p.lanes_per_warp < 0 || p.lanes_per_warp > 32 || p.time_arith < 0 || p.time_arith > 2) {
+    std::free(c);
+    return SR_EINVAL;
+  }
+  int rc_shape = SR_OK;
+  if (p.lanes_per_region == 32) {
     c->mode = 1;
     int wpb = p.threads_per_block ? p.threads_per_block : 4;   // warps per block
-    if (wpb > 8) wpb = 8;
+    if (wpb > 4) wpb = 4;                                     // the kernel's block limit
+    c->lanes = 1;
     c->rl = wpb;
     c->tpb = 32 * wpb;
     c->smem = 0;
-    int per_sm_blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<1>, c->tpb, 0) !=
-            cudaSuccess ||
-        per_sm_blocks < 1) {
-      free_all(c);
-      std::free(c);
-      return SR_EUNSUPPORTED;
-    }
-    int blocks = p.blocks ? p.blocks : (c->NR + wpb - 1) / wpb;
-    if (blocks > per_sm_blocks * c->num_sms) blocks = per_sm_blocks * c->num_sms;
-    c->blocks = blocks;
   } else {
-  c->mode = 0;
-  int rl = p.threads_per_block;
-  if (rl == 0) {
-    const int per_sm = (c->NR + c->num_sms - 1) / c->num_sms;
-    const int bps = (per_sm + 255) / 256;              // blocks per SM
-    rl = (per_sm + bps - 1) / bps;
-    if (rl > 32) rl = ((rl + 31) / 32) * 32;
-    if (rl > 256) rl = 256;
-    if (rl < 1) rl = 1;
+    int lanes = p.lanes_per_warp;
+    if (lanes == 0) {
+      lanes = (c->NR + 8 * c->num_sms - 1) / (8 * c->num_sms);   // about 8 warps per SM
+      if (lanes < 1) lanes = 1;
+      if (lanes > 32) lanes = 32;
+    }
+    const int soft = p.time_arith == 2 || (p.time_arith == 0 && lanes * 8 * c->num_sms < c->NR);
+    c->mode = soft ? 2 : 0;
+    c->lanes = lanes;
+    int wpb = p.threads_per_block ? (p.threads_per_block + lanes - 1) / lanes : 0;
+    if (wpb == 0) {
+      const int warps = (c->NR + lanes - 1) / lanes;
+      const int per_sm = (warps + c->num_sms - 1) / c->num_sms;
+      wpb = per_sm < 4 ? per_sm : 4;
+      if (wpb < 1) wpb = 1;
+    }
+    if (wpb > 8) wpb = 8;
+    c->rl = wpb * lanes;
+    c->tpb = 32 * wpb;
+    c->smem = (size_t)(H + 10) * c->rl * sizeof(uint32_t);
   }
-  if (rl > 256) rl = 256;
-  int tpb = p.block_threads ? p.block_threads : ((rl + 31) / 32) * 32;
-  if (!p.block_threads && tpb < 128) tpb = 128;
-  if (tpb < rl) tpb = rl;
-  if (tpb > 256) tpb = 256;
-  c->rl = rl;
-  c->tpb = tpb;
-  c->smem = (size_t)(H + 10) * rl * sizeof(uint32_t);
-  int per_sm_blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0>, tpb, c->smem) !=
-          cudaSuccess ||
-      per_sm_blocks < 1) {
+  {
+    const void* fn = c->mode == 1 ? (const void*)relax_kernel<1>
+                                  : (c->mode == 2 ? (const void*)relax_kernel<2> : (const void*)relax_kernel<0>);
+    cudaFuncAttributes fa;
+    int per_sm_blocks = 0;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || c->tpb > fa.maxThreadsPerBlock ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, fn, c->tpb, c->smem) != cudaSuccess ||
+        per_sm_blocks < 1) {
+      cudaGetLastError();
+      rc_shape = SR_EUNSUPPORTED;
+    } else {
+      int blocks = p.blocks ? p.blocks : (c->NR + c->rl - 1) / c->rl;
+      if (blocks > per_sm_blocks * c->num_sms) blocks = per_sm_blocks * c->num_sms;
+      c->blocks = blocks;
+    }
+  }
+  if (rc_shape != SR_OK) {
     free_all(c);
     std::free(c);
-    return SR_EUNSUPPORTED;
-  }
-  const int want = (c->NR + rl - 1) / rl;
-  int blocks = p.blocks ? p.blocks : want;
-  const int max_res = per_sm_blocks * c->num_sms;
-  if (blocks > max_res) blocks = max_res;
-  c->blocks = blocks;
+    return rc_shape;
   }
 
   const size_t nr = (size_t)c->NR;
@@ -2113,6 +2169,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   int tpb = ((rl + 31) / 32) * 32;
   if (tpb < 128) tpb = 128;
   c.rl = rl;
+  c.lanes = 32;            // lane mapping, every thread of a block a region lane
   c.tpb = tpb;
   c.smem = (size_t)(region_h + 10) * rl * sizeof(uint32_t);
   int per_sm_blocks = 0;

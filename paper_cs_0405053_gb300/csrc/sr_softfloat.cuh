@@ -174,7 +174,8 @@ __device__ __forceinline__ double div_pos(double a, double b) {
   const u64 D = B << 11;
   const float df = __uint2float_rn((unsigned)(D >> 40));          // exact, [2^23, 2^24)
   const float rf = __fdividef(1.0f, df);                          // ~2^-22 relative
-  u64 V = __float2ull_rz(rf * 1.5474250491067253e26f);             // rf * 2^87, saturating
+  // rf * 2^55 in [2^31, 2^32]: a 32-bit conversion (saturating), then << 32
+  u64 V = (u64)__float2uint_rz(rf * 36028797018963968.0f) << 32;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     // E = 2^127 - D V (signed); V += V E / 2^127

@@ -95,7 +95,11 @@ def test_rate_table_matches():
 
 
 # ----------------------------------------------------------------- trajectories
-LPR = [1, 32]     # one lane per region, one warp per region
+# mappings: (lanes per region, region lanes per warp, time arithmetic)
+MAPS = [dict(lanes_per_region=1, lanes_per_warp=32, time_arith=1),
+        dict(lanes_per_region=1, lanes_per_warp=3, time_arith=2),
+        dict(lanes_per_region=32)]
+LPR = list(range(len(MAPS)))
 
 
 @pytest.mark.parametrize("lpr", LPR)
@@ -103,7 +107,7 @@ LPR = [1, 32]     # one lane per region, one warp per region
                                    (16, 16, 4), (16, 4, 16), (16, 1, 16), (9, 3, 1), (32, 8, 8),
                                    (30, 10, 6), (32, 32, 32), (64, 32, 32)])
 def test_small_lattices_bit_exact(L, W, H, lpr):
-    _compare(L, W, H, seed=L * 31 + W, T=1.7, Tw=0.7, nwin=4, lanes_per_region=lpr)
+    _compare(L, W, H, seed=L * 31 + W, T=1.7, Tw=0.7, nwin=4, **MAPS[lpr])
 
 
 @pytest.mark.parametrize("T,h,J,rates,init", [(1.0, 0.0, 1.0, "metropolis", "fair"),
@@ -116,7 +120,7 @@ def test_small_lattices_bit_exact(L, W, H, lpr):
 @pytest.mark.parametrize("lpr", LPR)
 def test_parameters_bit_exact(T, h, J, rates, init, lpr):
     _compare(24, 8, 6, J=J, h=h, T=T, rates=rates, init=init, seed=5, Tw=0.5, nwin=4,
-             lanes_per_region=lpr)
+             **MAPS[lpr])
 
 
 def test_given_initial_spins():
@@ -130,7 +134,7 @@ def test_given_initial_spins():
 def test_small_config_L64_bit_exact(seed, lpr):
     """L = 64, 4 x 4 regions of 16 x 16, J = 1, h = 0.05, T = 1.5, fair coin,
     window 1.0, run to t = 10."""
-    _compare(64, 16, 16, h=0.05, T=1.5, seed=seed, Tw=1.0, nwin=10, lanes_per_region=lpr)
+    _compare(64, 16, 16, h=0.05, T=1.5, seed=seed, Tw=1.0, nwin=10, **MAPS[lpr])
 
 
 def test_window_length_does_not_change_the_trajectory():
@@ -182,12 +186,12 @@ def test_iterations_follow_the_canonical_assumption():
 
 @pytest.mark.parametrize("lpr", LPR)
 def test_medium_lattice_bit_exact(lpr):
-    _compare(256, 16, 16, h=0.05, T=1.0, seed=1, Tw=1.0, nwin=3, trace=False, lanes_per_region=lpr)
+    _compare(256, 16, 16, h=0.05, T=1.0, seed=1, Tw=1.0, nwin=3, trace=False, **MAPS[lpr])
 
 
 @pytest.mark.parametrize("lpr", LPR)
 def test_capacity_growth_exact_both_mappings(lpr):
-    _compare(64, 16, 16, T=3.5, seed=6, Tw=2.0, nwin=2, lanes_per_region=lpr)
+    _compare(64, 16, 16, T=3.5, seed=6, Tw=2.0, nwin=2, **MAPS[lpr])
 
 
 # ----------------------------------------------------------------- failure paths
