@@ -135,6 +135,8 @@ __device__ __noinline__ bool grid_barrier(DevStats* st, long long timeout) {
 struct Region {
   uint32_t* rows;   // rows[y * stride]
   uint32_t* N;      // N[k * stride]
+  uint32_t* C;      // C[(k * hq + y/4) * stride]: byte y%4 = sites of class k in row y
+  int hq;           // count words per class, (H + 3) / 4
   int stride;
   int W, H;
   bool spans_x, spans_y;   // the region covers the whole periodic extent
@@ -203,9 +205,12 @@ __device__ __forceinline__ uint32_t eq_count(uint32_t s0, uint32_t s1, uint32_t 
 // Class change of one site: N_k and Lambda follow (§3: "each spin flip changes
 // the class membership of several atoms").
 __device__ __forceinline__ void move_class(const Region& g, const KParams& p, int from, int to,
-                                           unsigned long long& lam) {
+                                           int y, unsigned long long& lam) {
   g.N[from * g.stride] -= 1u;
   g.N[to * g.stride] += 1u;
+  const uint32_t one = 1u << (8 * (y & 3));
+  g.C[(from * g.hq + (y >> 2)) * g.stride] -= one;
+  g.C[(to * g.hq + (y >> 2)) * g.stride] += one;
   lam = lam - p.P[from] + p.P[to];
 }
 
@@ -382,20 +387,31 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
   }
 
   // ---- class counts N_k, Lambda, and the region's spin / owned-bond sums
-  unsigned Nk[10];
+  unsigned Nk[10], cw[10];
 #pragma unroll
-  for (int k = 0; k < 10; ++k) Nk[k] = 0;
+  for (int k = 0; k < 10; ++k) Nk[k] = cw[k] = 0;
   int mag0 = 0, bond0 = 0;
   for (int y = 0; y < H; ++y) {
     const uint32_t rw = g.row(y);
     uint32_t up, dn, lf, rt, s0, s1, s2;
     g.nbr_words(y, rw, up, dn, lf, rt);
     add4(up, dn, lf, rt, s0, s1, s2);
+    const int sh = 8 * (y & 3);
 #pragma unroll
     for (int n = 0; n < 5; ++n) {
       const uint32_t e = eq_count(s0, s1, s2, n) & g.wmask;
-      Nk[5 + n] += __popc(e & rw);
-      Nk[n] += __popc(e & ~rw);
+      const unsigned cu = __popc(e & rw), cd = __popc(e & ~rw);
+      Nk[5 + n] += cu;
+      Nk[n] += cd;
+      cw[5 + n] |= cu << sh;
+      cw[n] |= cd << sh;
+    }
+    if ((y & 3) == 3 || y == H - 1) {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        g.C[(k * g.hq + (y >> 2)) * g.stride] = cw[k];
+        cw[k] = 0;
+      }
     }
     mag0 += 2 * __popc(rw) - W;
     bond0 += (W - 2 * __popc((rw ^ rt) & g.wmask)) + (W - 2 * __popc((rw ^ dn) & g.wmask));
@@ -480,23 +496,32 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       unsigned long long j = class_pos(q53 - Aprev, p.P[ks], p.Rp[ks]);
       if (j >= Nks) j = Nks - 1;
       unsigned jj = (unsigned)j;
-      // the jj-th class-k* site in row-major order (linear order of §3, Phase 3)
+      // the jj-th class-k* site in row-major order (linear order of §3, Phase 3):
+      // the row from the per-row counts of class k*, then the site in that row
       const int sp = ks >= 5;
       const int nn = ks - 5 * sp;
       int fx = 0, fy = 0;
-      for (int y = 0; y < H; ++y) {
-        const uint32_t rw = g.row(y);
-        uint32_t up, dn, lf, rt, s0, s1, s2;
-        g.nbr_words(y, rw, up, dn, lf, rt);
-        add4(up, dn, lf, rt, s0, s1, s2);
-        const uint32_t m = eq_count(s0, s1, s2, nn) & (sp ? rw : ~rw) & g.wmask;
-        const unsigned c = __popc(m);
-        if (jj < c) {
-          fx = nth_set_bit(m, jj);
-          fy = y;
+      for (int qd = 0; qd < g.hq; ++qd) {
+        const uint32_t w = g.C[(ks * g.hq + qd) * g.stride];
+        const unsigned s4 = __vsadu4(w, 0u);        // sites of class k* in these 4 rows
+        if (jj < s4) {
+          int u = 0;
+          for (; u < 3; ++u) {
+            const unsigned cy = (w >> (8 * u)) & 0xFFu;
+            if (jj < cy) break;
+            jj -= cy;
+          }
+          fy = 4 * qd + u;
           break;
         }
-        jj -= c;
+        jj -= s4;
+      }
+      {
+        const uint32_t rw = g.row(fy);
+        uint32_t up, dn, lf, rt, s0, s1, s2;
+        g.nbr_words(fy, rw, up, dn, lf, rt);
+        add4(up, dn, lf, rt, s0, s1, s2);
+        fx = nth_set_bit(eq_count(s0, s1, s2, nn) & (sp ? rw : ~rw) & g.wmask, jj);
       }
       // ---- flip (fx, fy); classes of the site and its in-region neighbours
       const int cv = g.class_at(fx, fy);
@@ -510,8 +535,8 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       if (fy > 0 || g.spans_y) { nbx[nnb] = fx; nby[nnb] = (fy == 0) ? H - 1 : fy - 1; ++nnb; }
       for (int a = 0; a < nnb; ++a) nbc[a] = g.class_at(nbx[a], nby[a]);
       g.rows[fy * g.stride] ^= (1u << fx);
-      move_class(g, p, cv, cv + (s_old ? -5 : 5), lam);
-      for (int a = 0; a < nnb; ++a) move_class(g, p, nbc[a], nbc[a] + dnb, lam);
+      move_class(g, p, cv, cv + (s_old ? -5 : 5), fy, lam);
+      for (int a = 0; a < nnb; ++a) move_class(g, p, nbc[a], nbc[a] + dnb, nby[a], lam);
 
       // observables: dM = 2 sig, dBonds = 4 beta (Eq. 2.1 book-keeping)
       const int sig = s_old ? -1 : 1;
@@ -591,7 +616,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       // class of the adjacent site after the change; before it, its up count
       // differed by one
       const int cu_new = g.class_at(ux, uy);
-      move_class(g, p, cu_new + (up_now ? -1 : 1), cu_new, lam);
+      move_class(g, p, cu_new + (up_now ? -1 : 1), cu_new, uy, lam);
       // advance the cursor of direction db
       const unsigned nidx = idx[db] + 1;
       idx[db] = nidx;
@@ -1146,6 +1171,8 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : 256, MODE == 1 ? SR_WARP_MIN
   const int stride = p.rl;
   g.rows = smem + (LANES && is_slot ? slot : 0);
   g.N = smem + p.H * stride + (LANES && is_slot ? slot : 0);
+  g.hq = (p.H + 3) / 4;
+  g.C = smem + (p.H + 10) * stride + (LANES && is_slot ? slot : 0);
   g.stride = stride;
   g.W = p.W;
   g.H = p.H;
@@ -1523,6 +1550,18 @@ int alloc_history(sr_ctx* c, int cap) {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SR_OK : SR_ECUDA; }
 
+// Shared memory of a lane-mapping block: per region slot, H spin rows, ten
+// class counts and ten class-by-row count groups of ceil(H/4) words.
+size_t lane_smem_bytes(int H, int slots) {
+  return (size_t)(H + 10 + 10 * ((H + 3) / 4)) * (size_t)slots * sizeof(uint32_t);
+}
+
+// Allow a kernel more than the default 48 KB of dynamic shared memory.
+bool allow_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
+
 // Initial state: rows (copy 0) come from the caller or the init kernel.
 int init_state(sr_ctx* c, const int8_t* dev_spins) {
   KParams k = make_params(c);
@@ -1709,14 +1748,15 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
     if (wpb > 8) wpb = 8;
     c->rl = wpb * lanes;
     c->tpb = 32 * wpb;
-    c->smem = (size_t)(H + 10) * c->rl * sizeof(uint32_t);
+    c->smem = lane_smem_bytes(H, c->rl);
   }
   {
     const void* fn = c->mode == 1 ? (const void*)relax_kernel<1>
                                   : (c->mode == 2 ? (const void*)relax_kernel<2> : (const void*)relax_kernel<0>);
     cudaFuncAttributes fa;
     int per_sm_blocks = 0;
-    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || c->tpb > fa.maxThreadsPerBlock ||
+    if (!allow_smem(fn, c->smem) || cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
+        c->tpb > fa.maxThreadsPerBlock ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, fn, c->tpb, c->smem) != cudaSuccess ||
         per_sm_blocks < 1) {
       cudaGetLastError();
@@ -2171,12 +2211,15 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.rl = rl;
   c.lanes = 32;            // lane mapping, every thread of a block a region lane
   c.tpb = tpb;
-  c.smem = (size_t)(region_h + 10) * rl * sizeof(uint32_t);
+  c.smem = lane_smem_bytes(region_h, rl);
   int per_sm_blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0>, tpb, c.smem) !=
+  if (!allow_smem((const void*)relax_kernel<0>, c.smem) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0>, tpb, c.smem) !=
           cudaSuccess ||
-      per_sm_blocks < 1)
+      per_sm_blocks < 1) {
+    cudaGetLastError();
     return SR_EUNSUPPORTED;
+  }
   int blocks = (c.NR + rl - 1) / rl;
   if (blocks > per_sm_blocks * c.num_sms) blocks = per_sm_blocks * c.num_sms;
   c.blocks = blocks;
