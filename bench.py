@@ -296,7 +296,7 @@ def run_profile_case(args):
     import paper_cs_0405053_gb300 as sr
     torch.cuda.set_device(0)
     lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=1, lanes_per_region=args.lpr,
-                     lanes_per_warp=args.lpw, time_arith=args.arith)
+                     lanes_per_warp=args.lpw, time_arith=args.arith, replay_records=args.replay)
     t0 = None
     for _ in range(args.warmup):
         lat.reset()
@@ -311,6 +311,7 @@ def run_profile_case(args):
     mhz = 2070.0
     print(json.dumps({"profile_case": True, "tw": args.tw, "windows": args.windows,
                       "lanes_per_region": args.lpr, "lanes_per_warp": args.lpw, "arith": args.arith,
+                      "replay": args.replay,
                       "blocks": lat.blocks, "ms": dt * 1e3,
                       "committed": o.committed, "generated": o.generated,
                       "iterations": o.iterations, "passes": o.region_passes,
@@ -334,6 +335,8 @@ def main():
                     help="lanes per region: 1, 32 or 0 (automatic)")
     ap.add_argument("--lpw", type=int, default=0, help="region lanes per warp (lane mapping)")
     ap.add_argument("--arith", type=int, default=0, help="time arithmetic: 1 FP64, 2 integer")
+    ap.add_argument("--replay", type=int, default=0,
+                    help="checkpoint records per region for incremental replay (0 auto, -1 off)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

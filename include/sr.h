@@ -80,6 +80,9 @@ typedef struct sr_params {
                                    draw the presimulated random pairs; 0 = automatic */
   int blocks;                   /* 0 = automatic (all regions resident if they fit) */
   int barrier_timeout_ms;       /* bound on each grid-wide wait; 0 = 2000 */
+  int replay_records;           /* incremental replay (one lane per region): checkpoints kept per
+                                   region of the break points consumed in a pass, so the next pass
+                                   restarts after its last unchanged input; 0 = 64, -1 = off */
   int test_barrier_skip_block;  /* test hook: this block never arrives at a barrier; -1 = off */
   void* stream;                 /* cudaStream_t; NULL = the library creates its own */
 } sr_params;

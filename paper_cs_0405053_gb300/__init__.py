@@ -39,7 +39,8 @@ class _Params(C.Structure):
                 ("max_iters", C.c_int), ("trace_capacity", C.c_int),
                 ("lanes_per_region", C.c_int), ("lanes_per_warp", C.c_int), ("time_arith", C.c_int),
                 ("threads_per_block", C.c_int), ("block_threads", C.c_int), ("blocks", C.c_int),
-                ("barrier_timeout_ms", C.c_int), ("test_barrier_skip_block", C.c_int),
+                ("barrier_timeout_ms", C.c_int), ("replay_records", C.c_int),
+                ("test_barrier_skip_block", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -169,7 +170,8 @@ class Lattice:
                  time_arith: int = 0, threads_per_block: int = 0,
                  block_threads: int = 0,
                  blocks: int = 0,
-                 barrier_timeout_ms: int = 0, test_barrier_skip_block: int = -1,
+                 barrier_timeout_ms: int = 0, replay_records: int = 0,
+                 test_barrier_skip_block: int = -1,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
         lib = library()
         if stream is None and use_torch_stream:
@@ -182,7 +184,7 @@ class Lattice:
                       capacity, max_iters, trace_capacity, lanes_per_region, lanes_per_warp,
                       time_arith, threads_per_block,
                       block_threads, blocks,
-                      barrier_timeout_ms, test_barrier_skip_block, stream)
+                      barrier_timeout_ms, replay_records, test_barrier_skip_block, stream)
         self._ctx = _P()
         _check(lib.sr_create_ex(C.byref(self._ctx), C.byref(prm)), "sr_create_ex")
         n_regions = C.c_int()

@@ -85,6 +85,9 @@ struct KParams {
   unsigned long long* rkv;      // [K][NR]      presimulated V bits
   unsigned long long* rhi;      // [NR]         ring holds events [committed index, rhi)
   int K;                        // ring length (power of two)
+  uint32_t* log;                // [NR][CB][kRecHead + H] checkpoints of consumed break points
+  uint32_t* loghdr;             // [NR][4] breaks consumed, records kept, window-start sums
+  int CB;                       // checkpoint records per region (0 = no incremental replay)
   int rl;                       // region slots per block (the other threads only help fill)
   int lanes;                    // lane mappings: region lanes in each warp
   DevStats* st;
@@ -94,6 +97,9 @@ struct KParams {
   long long timeout_cycles;
   int skip_block;
 };
+
+// Words of a checkpoint record before the spin rows (see run_region).
+constexpr int kRecHead = 24;
 
 // ---------------------------------------------------------------- barrier
 // Grid-wide "synchronize" with a bounded wait (SR_TIMEOUT instead of a hang).
@@ -336,47 +342,160 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
   // ---- a region whose neighbours' lists did not change in the last iteration
   // sees the same input as then, so its output is the same: keep the
   // tentative state and carry the lists over instead of replaying the window
+  // same output as the last iteration: keep the tentative state, carry the lists over
+  auto carry_over = [&]() {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (!has[e]) continue;
+      const unsigned n = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
+      for (unsigned j = 0; j < n; ++j) {
+        const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
+        const size_t dst = (((size_t)wp * 4 + e) * cap + j) * nr + r;
+        p.ht[dst] = __ldcg(&p.ht[src]);
+        p.hp[dst] = __ldcg(&p.hp[src]);
+      }
+      p.hl[((size_t)wp * 4 + e) * nr + r] = n;
+    }
+    p.chg[(size_t)wp * nr + r] = 0;
+    acc.skips += 1;
+  };
   if (n_iter >= 2) {
     bool dirty = false;
 #pragma unroll
     for (int d = 0; d < 4; ++d)
       if (has[d] && __ldcg(&p.chg[(size_t)rp * nr + q[d]])) dirty = true;
     if (!dirty) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (!has[e]) continue;
-        const unsigned n = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
-        for (unsigned j = 0; j < n; ++j) {
-          const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
-          const size_t dst = (((size_t)wp * 4 + e) * cap + j) * nr + r;
-          p.ht[dst] = __ldcg(&p.ht[src]);
-          p.hp[dst] = __ldcg(&p.hp[src]);
-        }
-        p.hl[((size_t)wp * 4 + e) * nr + r] = n;
-      }
-      p.chg[(size_t)wp * nr + r] = 0;
-      acc.skips += 1;
+      carry_over();
       return;
     }
   }
+
+  // ---- incoming boundary lists: the neighbours' lists of the previous iteration;
+  // my N halo is fed by the N neighbour's S list, etc.
+  const double INF = __longlong_as_double(0x7FF0000000000000ll);
+  const int ein[4] = {1, 0, 3, 2};
+  unsigned len[4], idx[4];
+  double nt[4];
+  unsigned npos[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    len[d] = has[d] ? __ldcg(&p.hl[((size_t)rp * 4 + ein[d]) * nr + q[d]]) : 0u;
+    idx[d] = 0;
+    if (len[d] > 0) {
+      const size_t a = (((size_t)rp * 4 + ein[d]) * cap) * nr + q[d];
+      nt[d] = __ldcg(&p.ht[a]);
+      npos[d] = __ldcg(&p.hp[a]);
+    } else {
+      nt[d] = INF;
+      npos[d] = 0;
+    }
+  }
+  auto next_break = [&](long long& tbb, int& db) {   // ties: lower direction first
+    tbb = __double_as_longlong(nt[0]);
+    db = 0;
+#pragma unroll
+    for (int d = 1; d < 4; ++d) {
+      const long long v = __double_as_longlong(nt[d]);
+      if (v < tbb) { tbb = v; db = d; }
+    }
+  };
+  auto advance = [&](int db) {
+    const unsigned nidx = idx[db] + 1;
+    idx[db] = nidx;
+    if (nidx < len[db]) {
+      const size_t a = (((size_t)rp * 4 + ein[db]) * cap + nidx) * nr + q[db];
+      nt[db] = __ldcg(&p.ht[a]);
+      npos[db] = __ldcg(&p.hp[a]);
+    } else {
+      nt[db] = INF;
+    }
+  };
+
+  // ---- incremental replay: the state of this region after its m-th consumed
+  // break point depends only on the committed state and on its first m inputs.
+  // Walk the new inputs against the inputs logged by the last pass; resume from
+  // the checkpoint before the first difference.
+  const size_t rwords = (size_t)kRecHead + H;
+  uint32_t* rec0 = p.log + (size_t)r * p.CB * rwords;
+  uint32_t* hdr = p.loghdr + (size_t)r * 4;     // breaks consumed, records kept, M0, bonds0
+  unsigned m = 0;
+  if (n_iter >= 2 && p.CB > 0) {
+    const unsigned nb_total = hdr[0], nb_log = hdr[1];
+    long long tbb;
+    int db;
+    while (m < nb_log) {
+      next_break(tbb, db);
+      const uint32_t* rec = rec0 + (size_t)m * rwords;
+      const long long rt = (long long)(((unsigned long long)rec[1] << 32) | rec[0]);
+      if (tbb != rt || rec[2] != (npos[db] | ((unsigned)db << 8))) break;
+      advance(db);
+      ++m;
+    }
+    next_break(tbb, db);
+    if (m == nb_total && m == nb_log && tbb == 0x7FF0000000000000ll) {
+      carry_over();          // every input is the one the last pass consumed
+      return;
+    }
+  }
+  const bool resume = m > 0;
   acc.passes += 1;
 
-  // ---- committed state
-  const uint32_t* rows_c = p.rows + (size_t)cidx * H * nr;
-  for (int y = 0; y < H; ++y) g.rows[y * g.stride] = rows_c[(size_t)y * nr + r];
-  g.hN = p.halo[0 * nr + r];
-  g.hS = p.halo[1 * nr + r];
-  g.hW = p.halo[2 * nr + r];
-  g.hE = p.halo[3 * nr + r];
-  unsigned long long i = p.ci[cidx * nr + r];
-  double x = p.cx[cidx * nr + r];
-  unsigned long long kv = p.ckv[cidx * nr + r];
-  double b = p.cb[cidx * nr + r];
-  double tl = p.ct[cidx * nr + r];
+  unsigned long long i;
+  double x, b, tl;
+  unsigned long long kv;
+  unsigned olen[4] = {0u, 0u, 0u, 0u};
+  unsigned bevents = 0;
+  int ksig = 0, kbeta = 0;
+  Acc128 ssig = {0ull, 0}, sbeta = {0ull, 0};
+  const unsigned long long i_win = p.ci[cidx * nr + r];   // first event of the window
+  if (resume) {
+    // ---- state after the m-th consumed break of the last pass
+    const uint32_t* rec = rec0 + (size_t)(m - 1) * rwords;
+    tl = __longlong_as_double((long long)(((unsigned long long)rec[1] << 32) | rec[0]));
+    i = ((unsigned long long)rec[4] << 32) | rec[3];
+    b = __longlong_as_double((long long)(((unsigned long long)rec[6] << 32) | rec[5]));
+    olen[0] = rec[7] & 0xFFFFu;
+    olen[1] = rec[7] >> 16;
+    olen[2] = rec[8] & 0xFFFFu;
+    olen[3] = rec[8] >> 16;
+    bevents = rec[9];
+    ksig = (int)rec[10];
+    kbeta = (int)rec[11];
+    ssig.lo = ((unsigned long long)rec[13] << 32) | rec[12];
+    ssig.hi = (long long)(((unsigned long long)rec[15] << 32) | rec[14]);
+    sbeta.lo = ((unsigned long long)rec[17] << 32) | rec[16];
+    sbeta.hi = (long long)(((unsigned long long)rec[19] << 32) | rec[18]);
+    g.hN = rec[20];
+    g.hS = rec[21];
+    g.hW = rec[22];
+    g.hE = rec[23];
+    for (int y = 0; y < H; ++y) g.rows[y * g.stride] = rec[kRecHead + y];
+  } else {
+    // ---- committed state
+    const uint32_t* rows_c = p.rows + (size_t)cidx * H * nr;
+    for (int y = 0; y < H; ++y) g.rows[y * g.stride] = rows_c[(size_t)y * nr + r];
+    g.hN = p.halo[0 * nr + r];
+    g.hS = p.halo[1 * nr + r];
+    g.hW = p.halo[2 * nr + r];
+    g.hE = p.halo[3 * nr + r];
+    i = i_win;
+    b = p.cb[cidx * nr + r];
+    tl = p.ct[cidx * nr + r];
+  }
   // presimulated pairs (U, V) of the coming events (§4: the random numbers
   // as a list drawn before use); the pair of event i+1 is loaded one event ahead
   const unsigned long long hi = p.rhi[r];
   const unsigned long long kmask = (unsigned long long)p.K - 1ull;
+  if (!resume) {
+    x = p.cx[cidx * nr + r];
+    kv = p.ckv[cidx * nr + r];
+  } else if (i < hi) {
+    const size_t a = (size_t)(i & kmask) * nr + r;
+    x = p.rx[a];
+    kv = p.rkv[a];
+  } else {
+    draw_event(i, (uint32_t)r, p.key0, p.key1, x, kv);
+  }
   double px = 0.0;
   unsigned long long pkv = 0ull;
   bool pvalid = (i + 1ull) < hi;
@@ -422,56 +541,45 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
     g.N[k * g.stride] = Nk[k];
     lam += (unsigned long long)Nk[k] * p.P[k];
   }
-
-  // ---- incoming boundary lists: the neighbours' lists of the previous iteration;
-  // my N halo is fed by the N neighbour's S list, etc.
-  const double INF = __longlong_as_double(0x7FF0000000000000ll);
-  const int ein[4] = {1, 0, 3, 2};
-  unsigned len[4], idx[4];
-  double nt[4];
-  unsigned npos[4];
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    len[d] = has[d] ? __ldcg(&p.hl[((size_t)rp * 4 + ein[d]) * nr + q[d]]) : 0u;
-    idx[d] = 0;
-    if (len[d] > 0) {
-      const size_t a = (((size_t)rp * 4 + ein[d]) * cap) * nr + q[d];
-      nt[d] = __ldcg(&p.ht[a]);
-      npos[d] = __ldcg(&p.hp[a]);
-    } else {
-      nt[d] = INF;
-      npos[d] = 0;
-    }
+  if (resume) {                      // window-start sums, kept since the first pass
+    mag0 = (int)hdr[2];
+    bond0 = (int)hdr[3];
+  } else if (p.CB > 0) {
+    hdr[2] = (uint32_t)mag0;
+    hdr[3] = (uint32_t)bond0;
   }
-  // own lists: previous lengths for the comparison (§4, statement (c))
-  unsigned plen[4], olen[4];
+
+  // own lists: previous lengths for the comparison (§4, statement (c)); on a
+  // resumed pass the entries before the checkpoint are the same as last time
+  unsigned plen[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     plen[e] = has[e] ? __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]) : 0u;
-    olen[e] = 0;
+    if (resume && has[e]) {
+      for (unsigned j = 0; j < olen[e]; ++j) {
+        const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
+        const size_t dst = (((size_t)wp * 4 + e) * cap + j) * nr + r;
+        p.ht[dst] = __ldcg(&p.ht[src]);
+        p.hp[dst] = __ldcg(&p.hp[src]);
+      }
+    }
   }
 
   bool changed = false, overflow = false;
   unsigned long long events = 0, brk = 0;
-  unsigned bevents = 0;
-  int ksig = 0, kbeta = 0;
+  unsigned nrec = m, nbt = m;           // checkpoint records kept, breaks consumed
   // window integrals of the observables in fixed point (times as multiples of 2^-frac)
   const int frac = 62 - (int)((((unsigned long long)__double_as_longlong(t_end)) >> 52) - 1022);
-  Acc128 ssig = {0ull, 0}, sbeta = {0ull, 0};
   const uint32_t gx0 = (uint32_t)(rx * W), gy0 = (uint32_t)(ry * H);
   const long long tend_b = __double_as_longlong(t_end);
 
   // times are >= 0, so their bit patterns order like their values
   double tau = tau_any<SOFT>(tl, x, b, lam, p);
   for (;;) {
-    // earliest pending break point (ties: any order, a zero-length segment adds +0)
-    long long tbb = __double_as_longlong(nt[0]);
-    int db = 0;
-#pragma unroll
-    for (int d = 1; d < 4; ++d) {
-      const long long v = __double_as_longlong(nt[d]);
-      if (v < tbb) { tbb = v; db = d; }
-    }
+    // earliest pending break point
+    long long tbb;
+    int db;
+    next_break(tbb, db);
     const double tb = __longlong_as_double(tbb);
     const long long taub = __double_as_longlong(tau);
 
@@ -617,16 +725,39 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       // differed by one
       const int cu_new = g.class_at(ux, uy);
       move_class(g, p, cu_new + (up_now ? -1 : 1), cu_new, uy, lam);
-      // advance the cursor of direction db
-      const unsigned nidx = idx[db] + 1;
-      idx[db] = nidx;
-      if (nidx < len[db]) {
-        const size_t a = (((size_t)rp * 4 + ein[db]) * cap + nidx) * nr + q[db];
-        nt[db] = __ldcg(&p.ht[a]);
-        npos[db] = __ldcg(&p.hp[a]);
-      } else {
-        nt[db] = INF;
+      // checkpoint after this break point, for the next pass's replay
+      if (nrec < (unsigned)p.CB) {
+        uint32_t* rec = rec0 + (size_t)nrec * rwords;
+        rec[0] = (uint32_t)tbb;
+        rec[1] = (uint32_t)((unsigned long long)tbb >> 32);
+        rec[2] = pos | ((unsigned)db << 8);
+        rec[3] = (uint32_t)i;
+        rec[4] = (uint32_t)(i >> 32);
+        const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
+        rec[5] = (uint32_t)bb;
+        rec[6] = (uint32_t)(bb >> 32);
+        rec[7] = olen[0] | (olen[1] << 16);
+        rec[8] = olen[2] | (olen[3] << 16);
+        rec[9] = bevents;
+        rec[10] = (uint32_t)ksig;
+        rec[11] = (uint32_t)kbeta;
+        rec[12] = (uint32_t)ssig.lo;
+        rec[13] = (uint32_t)(ssig.lo >> 32);
+        rec[14] = (uint32_t)ssig.hi;
+        rec[15] = (uint32_t)((unsigned long long)ssig.hi >> 32);
+        rec[16] = (uint32_t)sbeta.lo;
+        rec[17] = (uint32_t)(sbeta.lo >> 32);
+        rec[18] = (uint32_t)sbeta.hi;
+        rec[19] = (uint32_t)((unsigned long long)sbeta.hi >> 32);
+        rec[20] = g.hN;
+        rec[21] = g.hS;
+        rec[22] = g.hW;
+        rec[23] = g.hE;
+        for (int y = 0; y < H; ++y) rec[kRecHead + y] = g.row(y);
+        ++nrec;
       }
+      ++nbt;
+      advance(db);
       ++brk;
     }
     tau = tau_any<SOFT>(tl, x, b, lam, p);
@@ -640,6 +771,10 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
     }
   }
   p.chg[(size_t)wp * nr + r] = (changed || overflow) ? 1 : 0;
+  if (p.CB > 0) {
+    hdr[0] = nbt;
+    hdr[1] = nrec;
+  }
   // ---- tentative end state
   const unsigned tc = cidx ^ 1u;
   uint32_t* rows_t = p.rows + (size_t)tc * H * nr;
@@ -661,7 +796,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
 
   acc.events += events;
   acc.breaks += brk;
-  if ((unsigned)events > acc.emax) acc.emax = (unsigned)events;
+  if ((unsigned)(i - i_win) > acc.emax) acc.emax = (unsigned)(i - i_win);
   if (bevents > acc.fmax) acc.fmax = bevents;
   acc.changed |= changed || overflow;
   acc.overflow |= overflow;
@@ -1149,12 +1284,19 @@ __device__ void fill_ring(const KParams& p, unsigned cidx) {
 #ifndef SR_WARP_MIN_BLOCKS
 #define SR_WARP_MIN_BLOCKS 7
 #endif
+#ifndef SR_LANE_MAX_THREADS
+#define SR_LANE_MAX_THREADS 256
+#endif
+#ifndef SR_LANE_MIN_BLOCKS
+#define SR_LANE_MIN_BLOCKS 2
+#endif
 // MODE 0 / 2: one lane per region with FP64 / integer-emulated time
 // arithmetic; the first `lanes` lanes of every warp are region lanes.  MODE 1:
 // one warp per region.  Region slot j of block b owns regions
 // b*rl + j + k*(gridDim.x*rl).
 template <int MODE>
-__global__ void __launch_bounds__(MODE == 1 ? 128 : 256, MODE == 1 ? SR_WARP_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
+                                   MODE == 1 ? SR_WARP_MIN_BLOCKS : SR_LANE_MIN_BLOCKS)
     relax_kernel(KParams p) {
   extern __shared__ uint32_t smem[];
   if ((int)blockIdx.x == p.skip_block) return;   // test hook: never reaches a barrier
@@ -1429,8 +1571,9 @@ struct sr_ctx {
   bool own_stream;
   int num_sms;
   int clock_khz;
-  uint32_t *rows, *halo, *hl, *trs, *win_iters;
+  uint32_t *rows, *halo, *hl, *trs, *win_iters, *log, *loghdr;
   uint8_t* chg;
+  int CB;
   unsigned long long *ci, *ckv, *rkv, *rhi;
   double* rx;
   int K, Kcap;
@@ -1516,6 +1659,9 @@ KParams make_params(const sr_ctx* c) {
   k.trt = c->trt;
   k.trs = c->trs;
   k.tcap = c->prm.trace_capacity;
+  k.log = c->log;
+  k.loghdr = c->loghdr;
+  k.CB = c->CB;
   k.rx = c->rx;
   k.rkv = c->rkv;
   k.rhi = c->rhi;
@@ -1633,7 +1779,7 @@ int set_ring(sr_ctx* c, int K) {
 void free_all(sr_ctx* c) {
   void* dev[] = {c->rows, c->halo, c->hl, c->trs, c->win_iters, c->ci, c->ckv, c->cx, c->cb,
                  c->ct, c->cim, c->cib, c->ht, c->trt, c->hp, c->st, c->obs_i, c->obs_f, c->stage,
-                 c->rx, c->rkv, c->rhi, c->chg};
+                 c->rx, c->rkv, c->rhi, c->chg, c->log, c->loghdr};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (c->h_st) cudaFreeHost(c->h_st);
@@ -1731,11 +1877,11 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   } else {
     int lanes = p.lanes_per_warp;
     if (lanes == 0) {
-      lanes = (c->NR + 8 * c->num_sms - 1) / (8 * c->num_sms);   // about 8 warps per SM
+      lanes = (c->NR + 16 * c->num_sms - 1) / (16 * c->num_sms);  // about 16 warps per SM
       if (lanes < 1) lanes = 1;
       if (lanes > 32) lanes = 32;
     }
-    const int soft = p.time_arith == 2 || (p.time_arith == 0 && lanes * 8 * c->num_sms < c->NR);
+    const int soft = p.time_arith == 2 || (p.time_arith == 0 && lanes * 16 * c->num_sms < c->NR);
     c->mode = soft ? 2 : 0;
     c->lanes = lanes;
     int wpb = p.threads_per_block ? (p.threads_per_block + lanes - 1) / lanes : 0;
@@ -1745,7 +1891,7 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
       wpb = per_sm < 4 ? per_sm : 4;
       if (wpb < 1) wpb = 1;
     }
-    if (wpb > 8) wpb = 8;
+    if (wpb > SR_LANE_MAX_THREADS / 32) wpb = SR_LANE_MAX_THREADS / 32;
     c->rl = wpb * lanes;
     c->tpb = 32 * wpb;
     c->smem = lane_smem_bytes(H, c->rl);
@@ -1791,6 +1937,12 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   rc |= dalloc(&c->stage, (size_t)p.L * p.L);
   rc |= dalloc(&c->rhi, nr);
   rc |= dalloc(&c->chg, 2 * nr);
+  // incremental replay log: lane mappings only
+  c->CB = (c->mode == 1 || p.replay_records < 0) ? 0 : (p.replay_records ? p.replay_records : 64);
+  if (c->CB > 0) {
+    rc |= dalloc(&c->log, nr * (size_t)c->CB * (size_t)(kRecHead + H));
+    rc |= dalloc(&c->loghdr, nr * 4);
+  }
   if (p.trace_capacity > 0) {
     rc |= dalloc(&c->trt, nr * (size_t)p.trace_capacity);
     rc |= dalloc(&c->trs, nr * (size_t)p.trace_capacity);
