@@ -35,14 +35,23 @@ WORKLOAD = ("L=1024 periodic 2D Ising, 64x64 regions of 16x16, J=1, h=0.05, T=1.
             "spins, Metropolis rates via the n-fold way, run to t=100 for each window length "
             "Tw in {0.25, 1, 4}")
 
-# FP64 pipe operations per committed event and per break point of the method
-# as formulated here (counted from the formulas; divisions counted in the
-# FP64-pipe slots one IEEE division takes on this part, measured 8.6).
-FP64_DIV_SLOTS = 8.6
-FP64_PER_EVENT = 28 + 2 * FP64_DIV_SLOTS + 8      # -log U (Horner, scale, ln2), tau, observables
-FP64_PER_BREAK = 6 + FP64_DIV_SLOTS               # accrual, new tau
-FP64_PEAK_OPS = 5.0e11                            # measured DFMA/DADD lane-ops/s, all 152 SMs
-HIST_BYTES_PER_BOUNDARY_EVENT = 9 * 2             # f64 time + u8 position, written once, read once
+# Algorithmic work of the method per committed event (counted from the formulas
+# of §3 and §5, independent of how this implementation executes them):
+#   Philox4x32-10 ~100 integer ops, uniform mapping 6, -log U ~25, the waiting
+#   time (sub, divide, add) ~10, Lambda and the class scan ~30, the site rank
+#   ~20, the class update of <= 5 sites ~60, the history record ~10
+# -> ~260 integer + ~50 floating-point operations = 310 operations; a break
+# point adds ~35 (hazard accrual, halo update, class update, new waiting time).
+OPS_PER_EVENT = 310
+OPS_PER_BREAK = 35
+# Integer issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz.
+SMS, LANES_PER_SM, SM_MHZ = 152, 128, 2070.0
+INT_PEAK_OPS = SMS * LANES_PER_SM * SM_MHZ * 1e6          # 4.03e13 lane-ops/s
+# History bytes per committed boundary event: f64 time + u8 position, written
+# once and read by one neighbour (two for a corner); the HBM bound uses the
+# measured copy bandwidth of this part.
+HIST_BYTES_PER_BOUNDARY_EVENT = 9 * 2
+HBM_GBS = 6788.3
 
 
 def _dist_env():
@@ -237,15 +246,17 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (the persistent relaxation kernel)
+    # ---- roofline of the dominant kernel (the persistent relaxation kernel):
+    # algorithmic integer work of the committed trajectory per launch / launch time
     kms = sum(kernel_ms) / len(kernel_ms)
     last = {Tw: per_tw[Tw][-1] for Tw in WINDOWS}
     ev_per_launch = statistics.mean(o.committed for (_, _, o, _) in (last[t] for t in WINDOWS))
-    brk_per_launch = statistics.mean(o.breaks / max(1, o.iterations) * o.last_iters
-                                     for (_, _, o, _) in (last[t] for t in WINDOWS))
-    fp64_ops = ev_per_launch * FP64_PER_EVENT
-    achieved = fp64_ops / (kms * 1e-3)
-    peak = FP64_PEAK_OPS
+    ops = ev_per_launch * OPS_PER_EVENT
+    achieved = ops / (kms * 1e-3)
+    peak = INT_PEAK_OPS
+    # the other bound of the statement: boundary history bytes at HBM bandwidth
+    # (boundary fraction of 16x16 regions at uniform rates, 60/256)
+    hbm_bound_events = HBM_GBS * 1e9 / (HIST_BYTES_PER_BOUNDARY_EVENT * 60 / 256)
     cpu_committed, cpu_dt = _oracle_baseline()
     tw_detail = {}
     for Tw in WINDOWS:
@@ -269,10 +280,12 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "per_window_length": tw_detail},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "pipe": "FP64 (measured DFMA/DADD rate of this part)",
+                     "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz integer issue",
                      "kernel": "relax_kernel", "kernel_ms_avg": kms,
-                     "fp64_ops_per_committed_event": FP64_PER_EVENT},
+                     "ops_per_committed_event": OPS_PER_EVENT,
+                     "events_per_s_bounds": {"integer_issue": peak / OPS_PER_EVENT,
+                                             "history_bytes_at_hbm": hbm_bound_events}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": L * L * len(WINDOWS),
                 "d2h_bytes_per_step": (L * L + 64) * len(WINDOWS)},
         "gpu_launches": launches,

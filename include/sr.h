@@ -87,6 +87,17 @@ typedef struct sr_params {
   void* stream;                 /* cudaStream_t; NULL = the library creates its own */
 } sr_params;
 
+/* One lattice of a batch (sr_create_batch): its own side, Hamiltonian,
+ * temperature, seed, initial spins and rates; the region shape and every
+ * other setting come from the sr_params given with the batch. */
+typedef struct sr_replica {
+  int L;                        /* side, a multiple of region_w and region_h, >= 3 */
+  double J, h, T;               /* Eq. 2.1 and the temperature of Eq. 2.2 / 2.3 */
+  uint64_t seed;                /* Philox key of this lattice's draws and fair-coin spins */
+  int init_mode;                /* SR_INIT_* */
+  int rates;                    /* SR_RATES_* */
+} sr_replica;
+
 /* Observables and counters (reduced over all regions at the committed time). */
 typedef struct sr_obs {
   double t_c;                   /* committed time (§4) */
@@ -145,8 +156,47 @@ int sr_run_window(sr_ctx* ctx, double t0, double Tw);
 int sr_run_windows(sr_ctx* ctx, double t0, double Tw, int n);
 
 /* Observables at the committed time; *out is caller-owned.  Errors: SR_EINVAL,
- * SR_ECUDA. */
+ * SR_ECUDA.  In a batch context: lattice 0 (the launch counters region_passes
+ * .. slots cover the whole batch). */
 int sr_observables(sr_ctx* ctx, sr_obs* out);
+
+/* ---- batches of independent lattices ----
+ * The paper simulates one lattice.  A batch holds n lattices that never
+ * interact; each follows the §4 procedure on its own, with its own windows,
+ * iterations and results, bit for bit the same as a context of its own with
+ * the same region shape.  All lattices share one persistent launch: their
+ * regions fill the GPU together, and each lattice commits as soon as its own
+ * boundary histories stop changing.  Region r of lattice b is global region
+ * off_b + r, off_b = sum of the region counts of lattices 0 .. b-1.
+ *
+ * The single-lattice calls act on a batch context as follows: sr_run_window(s)
+ * runs every lattice (t0 must equal every lattice's t_c); sr_reset resets
+ * every lattice; sr_observables, sr_get_spins(_device), sr_set_spins(_device),
+ * sr_get_carry, sr_get_trace, sr_get_window_iters and sr_get_info refer to
+ * lattice 0. */
+
+/* reps: n >= 1 caller-owned descriptors (copied); common: region shape and
+ * the settings of sr_params other than L, J, h, T, seed, init_mode, rates
+ * (ignored).  Errors: SR_EINVAL, SR_ENOMEM, SR_ECUDA, SR_EUNSUPPORTED. */
+int sr_create_batch(sr_ctx** out, const sr_replica* reps, int n, const sr_params* common);
+
+/* For every lattice b, n_windows[b] >= 0 windows of length Tw[b] (> 0 where
+ * n_windows[b] > 0) from its committed time, all in one persistent launch
+ * (more after a capacity growth, as in sr_run_windows).  Host arrays of n
+ * entries.  Errors as sr_run_windows; on error every lattice keeps the state of
+ * its last converged window. */
+int sr_run_batch(sr_ctx* ctx, const double* Tw, const int* n_windows);
+
+/* Observables of lattice `replica` (0 <= replica < n).  Errors: SR_EINVAL,
+ * SR_ECUDA. */
+int sr_observables_replica(sr_ctx* ctx, int replica, sr_obs* out);
+
+/* Committed spins of lattice `replica` into a host buffer of n = L_b^2 int8. */
+int sr_get_spins_replica(sr_ctx* ctx, int replica, int8_t* host_out, size_t n);
+
+/* Clock state of lattice `replica` as sr_get_carry, n = its region count. */
+int sr_get_carry_replica(sr_ctx* ctx, int replica, uint64_t* index, double* x, double* b,
+                         double* t_last, size_t n);
 
 /* Free everything; NULL-safe. */
 void sr_destroy(sr_ctx* ctx);

@@ -18,7 +18,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["SRError", "Lattice", "Observables", "library", "eval_draws", "SR_OK"]
+__all__ = ["SRError", "Lattice", "Batch", "Replica", "Observables", "library", "eval_draws",
+           "SR_OK"]
 
 SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA = 0, -1, -2, -3
 SR_NOT_CONVERGED, SR_CAPACITY, SR_TIMEOUT, SR_EUNSUPPORTED = -4, -5, -6, -7
@@ -42,6 +43,23 @@ class _Params(C.Structure):
                 ("barrier_timeout_ms", C.c_int), ("replay_records", C.c_int),
                 ("test_barrier_skip_block", C.c_int),
                 ("stream", C.c_void_p)]
+
+
+class _Replica(C.Structure):
+    _fields_ = [("L", C.c_int), ("J", C.c_double), ("h", C.c_double), ("T", C.c_double),
+                ("seed", C.c_uint64), ("init_mode", C.c_int), ("rates", C.c_int)]
+
+
+@dataclass
+class Replica:
+    """One lattice of a Batch."""
+    L: int
+    J: float = 1.0
+    h: float = 0.0
+    T: float = 1.0
+    seed: int = 1
+    init: str = "fair"
+    rates: str = "metropolis"
 
 
 class _Obs(C.Structure):
@@ -115,6 +133,11 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_get_info": (C.c_int, [_P, _P, _P, _P, _P, _P]),
             "sr_eval_softfloat": (C.c_int, [C.c_int, _P, _P, _P, C.c_size_t]),
             "sr_strerror": (C.c_char_p, [C.c_int]),
+            "sr_create_batch": (C.c_int, [C.POINTER(_P), _P, C.c_int, C.POINTER(_Params)]),
+            "sr_run_batch": (C.c_int, [_P, _P, _P]),
+            "sr_observables_replica": (C.c_int, [_P, C.c_int, C.POINTER(_Obs)]),
+            "sr_get_spins_replica": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
+            "sr_get_carry_replica": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_size_t]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -290,3 +313,96 @@ class Lattice:
         if m < 0:
             raise SRError(m, "sr_get_window_iters")
         return out[:m]
+
+
+class Batch:
+    """Independent lattices simulated together: every lattice follows the
+    synchronous-relaxation procedure on its own (own windows, iterations and
+    results, the same as a Lattice of its own), while their regions share one
+    persistent launch.  All lattices use one region shape."""
+
+    def __init__(self, replicas, region: Tuple[int, int] = (16, 16), capacity: int = 0,
+                 max_iters: int = 0, lanes_per_region: int = 0, lanes_per_warp: int = 0,
+                 time_arith: int = 0, threads_per_block: int = 0, blocks: int = 0,
+                 barrier_timeout_ms: int = 0, replay_records: int = 0,
+                 stream: Optional[int] = None, use_torch_stream: bool = True):
+        lib = library()
+        if stream is None and use_torch_stream:
+            stream = _torch_stream()
+        self.replicas = [r if isinstance(r, Replica) else Replica(**r) for r in replicas]
+        self.region = region
+        arr = (_Replica * len(self.replicas))(*[
+            _Replica(r.L, r.J, r.h, r.T, r.seed, INIT_MODES[r.init], RATES[r.rates])
+            for r in self.replicas])
+        prm = _Params(0, 0.0, 0.0, 0.0, region[0], region[1], 0, 0, 0, capacity, max_iters, 0,
+                      lanes_per_region, lanes_per_warp, time_arith, threads_per_block, 0, blocks,
+                      barrier_timeout_ms, replay_records, -1, stream)
+        self._arr = arr
+        self._ctx = _P()
+        _check(lib.sr_create_batch(C.byref(self._ctx), C.cast(arr, C.c_void_p), len(arr),
+                                   C.byref(prm)), "sr_create_batch")
+        tpb = C.c_int()
+        blk = C.c_int()
+        _check(lib.sr_get_info(self._ctx, None, None, None, C.byref(tpb), C.byref(blk)),
+               "sr_get_info")
+        self.threads_per_block = tpb.value
+        self.blocks = blk.value
+        self.t_c = np.zeros(len(self.replicas), dtype=np.float64)
+
+    def __len__(self) -> int:
+        return len(self.replicas)
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            library().sr_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, Tw, n_windows) -> None:
+        """n_windows[b] windows of length Tw[b] for every lattice b (scalars
+        broadcast), all in one persistent launch."""
+        n = len(self.replicas)
+        tw = np.ascontiguousarray(np.broadcast_to(np.asarray(Tw, dtype=np.float64), (n,)))
+        nw = np.ascontiguousarray(np.broadcast_to(np.asarray(n_windows, dtype=np.int32), (n,)))
+        code = library().sr_run_batch(self._ctx, _ptr(tw), _ptr(nw))
+        for b in range(n):
+            self.t_c[b] = self.observables(b).t_c
+        _check(code, "sr_run_batch")
+
+    def reset(self) -> None:
+        _check(library().sr_reset(self._ctx), "sr_reset")
+        self.t_c[:] = 0.0
+
+    def observables(self, b: int) -> Observables:
+        o = _Obs()
+        _check(library().sr_observables_replica(self._ctx, b, C.byref(o)), "sr_observables_replica")
+        return Observables(*[getattr(o, f) for f, _ in _Obs._fields_])
+
+    def spins(self, b: int) -> np.ndarray:
+        L = self.replicas[b].L
+        out = np.zeros((L, L), dtype=np.int8)
+        _check(library().sr_get_spins_replica(self._ctx, b, _ptr(out), out.size),
+               "sr_get_spins_replica")
+        return out
+
+    def carry(self, b: int):
+        r = self.replicas[b]
+        n = (r.L // self.region[0]) * (r.L // self.region[1])
+        i = np.zeros(n, dtype=np.uint64)
+        x = np.zeros(n, dtype=np.float64)
+        bb = np.zeros(n, dtype=np.float64)
+        t = np.zeros(n, dtype=np.float64)
+        _check(library().sr_get_carry_replica(self._ctx, b, _ptr(i), _ptr(x), _ptr(bb), _ptr(t), n),
+               "sr_get_carry_replica")
+        return i, x, bb, t

@@ -9,7 +9,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsr.so")
 SOURCES = [os.path.join(CSRC, "sr_lib.cu")]
-HEADERS = [os.path.join(CSRC, "sr_device.cuh"), os.path.join(ROOT, "include", "sr.h")]
+HEADERS = [os.path.join(CSRC, "sr_device.cuh"), os.path.join(CSRC, "sr_softfloat.cuh"),
+           os.path.join(ROOT, "include", "sr.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

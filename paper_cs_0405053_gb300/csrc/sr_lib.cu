@@ -38,17 +38,8 @@ struct DevStats {
   unsigned status;
   unsigned bar_count;
   unsigned bar_gen;
-  unsigned flags[3];
-  unsigned windows_done;
-  unsigned pad0;
+  unsigned active;              // lattices with windows left in this launch
   // persistent across launches
-  unsigned cidx;          // which copy of the double-buffered state is committed
-  unsigned max_f;
-  unsigned last_iters;
-  unsigned max_iters_seen;
-  unsigned max_win_events;      // most events one region committed in one window
-  unsigned pad1;
-  unsigned long long committed, generated, breaks, windows, iterations;
   unsigned long long region_passes, region_skips;   // region iterations run / skipped
   unsigned long long run_cycles, run_cycles_max;    // cycles region slots spent on their regions
   unsigned long long slots;                         // region slots that reported
@@ -56,14 +47,42 @@ struct DevStats {
 
 constexpr int kWinRing = 4096;
 
-struct KParams {
-  int L, W, H, NX, NY, NR;
-  int spans_x, spans_y;
-  unsigned long long P[10];
+// One lattice of a batch.  Every lattice of a launch shares the region shape;
+// its regions are numbered off .. off + NR - 1 in the global region index.
+struct RepDesc {
+  int L, NX, NY, NR;            // side, regions across, regions down, regions
+  int off;                      // global index of its first region
+  int spans_x, spans_y;         // a region covers the whole periodic extent
+  uint32_t key0, key1;          // seed
+  int nwin;                     // windows to run in the current launch
+  int init_mode;                // SR_INIT_* of sr_reset
+  double t0, Tw;                // committed time at the launch, window length
+  unsigned long long P[10];     // p_k on the 2^-F grid
   unsigned long long Rp[10];    // floor((2^64 - 1) / P[k]) (0 when P[k] = 0)
+};
+
+// Per-lattice counters.
+struct RepStats {
+  unsigned long long committed, generated, breaks, windows, iterations;
+  unsigned last_iters, max_iters_seen, max_f, max_win_events;
+  unsigned windows_done;        // windows committed in the current launch
+};
+
+struct KParams {
+  int W, H, NR;                 // region shape, regions of all lattices
+  int nrep;                     // lattices
+  const RepDesc* reps;
+  const uint32_t* rrep;         // [NR] lattice of each region
+  RepStats* rs;                 // [nrep]
+  uint32_t* rflags;             // [3][nrep] "some region's lists changed", one row per
+                                // iteration slot; cleared by the host before a launch
+  uint8_t* rcidx;               // [NR] committed copy of each region's state
+  uint32_t* rn;                 // [NR] iteration of the region's current window
+  uint32_t* rwin;               // [NR] windows the region committed in this launch
+  double* rts;                  // [NR] start of the region's current window
+  uint8_t* rfill;               // [NR] ring top-up pending
   double scale;                 // 2^-F
   int F;
-  uint32_t key0, key1;
   uint32_t* rows;               // [2][H][NR]   spin rows, bit x = site x of the row
   uint32_t* halo;               // [4][NR]      N, S, W, E halo words at t_c
   unsigned long long* ci;       // [2][NR]      index of the pending event
@@ -91,12 +110,39 @@ struct KParams {
   int rl;                       // region slots per block (the other threads only help fill)
   int lanes;                    // lane mappings: region lanes in each warp
   DevStats* st;
-  uint32_t* win_iters;          // [kWinRing]
-  double t0, Tw;
-  int nwin, max_iters;
+  uint32_t* win_iters;          // [kWinRing] iterations of each window of lattice 0
+  int max_iters;
   long long timeout_cycles;
   int skip_block;
 };
+
+// The lattice of region r.
+struct Lat {
+  const unsigned long long* P;
+  const unsigned long long* Rp;
+  int L, NX, NY, off, loc, rep;
+  bool spans_x, spans_y;
+  uint32_t key0, key1;
+};
+
+__device__ __forceinline__ Lat lat_of(const KParams& p, int r) {
+  Lat t;
+  const int b = (int)__ldg(&p.rrep[r]);
+  const RepDesc* d = p.reps + b;
+  t.rep = b;
+  t.L = d->L;
+  t.NX = d->NX;
+  t.NY = d->NY;
+  t.off = d->off;
+  t.loc = r - d->off;
+  t.spans_x = d->spans_x != 0;
+  t.spans_y = d->spans_y != 0;
+  t.key0 = d->key0;
+  t.key1 = d->key1;
+  t.P = d->P;
+  t.Rp = d->Rp;
+  return t;
+}
 
 // Words of a checkpoint record before the spin rows (see run_region).
 constexpr int kRecHead = 24;
@@ -210,14 +256,14 @@ __device__ __forceinline__ uint32_t eq_count(uint32_t s0, uint32_t s1, uint32_t 
 
 // Class change of one site: N_k and Lambda follow (§3: "each spin flip changes
 // the class membership of several atoms").
-__device__ __forceinline__ void move_class(const Region& g, const KParams& p, int from, int to,
-                                           int y, unsigned long long& lam) {
+__device__ __forceinline__ void move_class(const Region& g, const unsigned long long* P, int from,
+                                           int to, int y, unsigned long long& lam) {
   g.N[from * g.stride] -= 1u;
   g.N[to * g.stride] += 1u;
   const uint32_t one = 1u << (8 * (y & 3));
   g.C[(from * g.hq + (y >> 2)) * g.stride] -= one;
   g.C[(to * g.hq + (y >> 2)) * g.stride] += one;
-  lam = lam - p.P[from] + p.P[to];
+  lam = lam - P[from] + P[to];
 }
 
 // tau of Eq. 3.4 / 5.6 in integer-emulated doubles (same bits as tau_hat).
@@ -322,20 +368,22 @@ __device__ __forceinline__ double accrue_any(double b, double tb, double tl, uns
 }
 
 template <int SOFT>
-__device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, double t_s,
-                           double t_end, Region& g, Acc& acc) {
+__device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, unsigned cidx,
+                           double t_s, double t_end, Region& g, Acc& acc) {
   const int W = p.W, H = p.H, NR = p.NR;
   const int wp = n_iter & 1;
   const int rp = wp ^ 1;
-  const int rx = r % p.NX, ry = r / p.NX;
+  const int rx = lt.loc % lt.NX, ry = lt.loc / lt.NX;
   const size_t nr = (size_t)NR;
   const size_t cap = (size_t)p.cap;
+  g.spans_x = lt.spans_x;
+  g.spans_y = lt.spans_y;
 
-  // ---- neighbours: d = 0 N, 1 S, 2 W, 3 E
-  const int qN = ((ry + p.NY - 1) % p.NY) * p.NX + rx;
-  const int qS = ((ry + 1) % p.NY) * p.NX + rx;
-  const int qW = ry * p.NX + (rx + p.NX - 1) % p.NX;
-  const int qE = ry * p.NX + (rx + 1) % p.NX;
+  // ---- neighbours (global region indices): d = 0 N, 1 S, 2 W, 3 E
+  const int qN = lt.off + ((ry + lt.NY - 1) % lt.NY) * lt.NX + rx;
+  const int qS = lt.off + ((ry + 1) % lt.NY) * lt.NX + rx;
+  const int qW = lt.off + ry * lt.NX + (rx + lt.NX - 1) % lt.NX;
+  const int qE = lt.off + ry * lt.NX + (rx + 1) % lt.NX;
   int q[4] = {qN, qS, qW, qE};
   bool has[4] = {!g.spans_y, !g.spans_y, !g.spans_x, !g.spans_x};
 
@@ -379,7 +427,8 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
   unsigned npos[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
-    len[d] = has[d] ? __ldcg(&p.hl[((size_t)rp * 4 + ein[d]) * nr + q[d]]) : 0u;
+    // iteration 1: the canonical assumption, no neighbour flips (§5)
+    len[d] = (has[d] && n_iter >= 2) ? __ldcg(&p.hl[((size_t)rp * 4 + ein[d]) * nr + q[d]]) : 0u;
     idx[d] = 0;
     if (len[d] > 0) {
       const size_t a = (((size_t)rp * 4 + ein[d]) * cap) * nr + q[d];
@@ -494,7 +543,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
     x = p.rx[a];
     kv = p.rkv[a];
   } else {
-    draw_event(i, (uint32_t)r, p.key0, p.key1, x, kv);
+    draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
   }
   double px = 0.0;
   unsigned long long pkv = 0ull;
@@ -539,7 +588,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
     g.N[k * g.stride] = Nk[k];
-    lam += (unsigned long long)Nk[k] * p.P[k];
+    lam += (unsigned long long)Nk[k] * lt.P[k];
   }
   if (resume) {                      // window-start sums, kept since the first pass
     mag0 = (int)hdr[2];
@@ -554,7 +603,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
   unsigned plen[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    plen[e] = has[e] ? __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]) : 0u;
+    plen[e] = (has[e] && n_iter >= 2) ? __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]) : 0u;
     if (resume && has[e]) {
       for (unsigned j = 0; j < olen[e]; ++j) {
         const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
@@ -596,12 +645,12 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       int ks = 9;
       for (int k = 0; k < 10; ++k) {
         Aprev = A;
-        A += (unsigned long long)g.N[k * g.stride] * p.P[k];
+        A += (unsigned long long)g.N[k * g.stride] * lt.P[k];
         if (q53 < A || (q53 == A && exact)) { ks = k; break; }
       }
       // position within the class, Eqs. 3.7-3.8: floor((V*Lambda - A(k*-1)) / p_k*)
       const unsigned Nks = g.N[ks * g.stride];
-      unsigned long long j = class_pos(q53 - Aprev, p.P[ks], p.Rp[ks]);
+      unsigned long long j = class_pos(q53 - Aprev, lt.P[ks], lt.Rp[ks]);
       if (j >= Nks) j = Nks - 1;
       unsigned jj = (unsigned)j;
       // the jj-th class-k* site in row-major order (linear order of §3, Phase 3):
@@ -643,8 +692,8 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       if (fy > 0 || g.spans_y) { nbx[nnb] = fx; nby[nnb] = (fy == 0) ? H - 1 : fy - 1; ++nnb; }
       for (int a = 0; a < nnb; ++a) nbc[a] = g.class_at(nbx[a], nby[a]);
       g.rows[fy * g.stride] ^= (1u << fx);
-      move_class(g, p, cv, cv + (s_old ? -5 : 5), fy, lam);
-      for (int a = 0; a < nnb; ++a) move_class(g, p, nbc[a], nbc[a] + dnb, nby[a], lam);
+      move_class(g, lt.P, cv, cv + (s_old ? -5 : 5), fy, lam);
+      for (int a = 0; a < nnb; ++a) move_class(g, lt.P, nbc[a], nbc[a] + dnb, nby[a], lam);
 
       // observables: dM = 2 sig, dBonds = 4 beta (Eq. 2.1 book-keeping)
       const int sig = s_old ? -1 : 1;
@@ -691,7 +740,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       if (boundary) ++bevents;
       if (p.tcap > 0 && i < (unsigned long long)p.tcap) {
         p.trt[(size_t)r * p.tcap + i] = tau;
-        p.trs[(size_t)r * p.tcap + i] = (gy0 + fy) * (uint32_t)p.L + gx0 + fx;
+        p.trs[(size_t)r * p.tcap + i] = (gy0 + fy) * (uint32_t)lt.L + gx0 + fx;
       }
       ++events;
       if (overflow) break;
@@ -703,7 +752,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
         x = px;
         kv = pkv;
       } else {
-        draw_event(i, (uint32_t)r, p.key0, p.key1, x, kv);
+        draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
       }
       pvalid = (i + 1ull) < hi;
       if (pvalid) {
@@ -724,7 +773,7 @@ __device__ void run_region(const KParams& p, int r, int n_iter, unsigned cidx, d
       // class of the adjacent site after the change; before it, its up count
       // differed by one
       const int cu_new = g.class_at(ux, uy);
-      move_class(g, p, cu_new + (up_now ? -1 : 1), cu_new, uy, lam);
+      move_class(g, lt.P, cu_new + (up_now ? -1 : 1), cu_new, uy, lam);
       // checkpoint after this break point, for the next pass's replay
       if (nrec < (unsigned)p.CB) {
         uint32_t* rec = rec0 + (size_t)nrec * rwords;
@@ -829,15 +878,15 @@ __device__ __forceinline__ long long shfl_xor_s64(long long v, int m) {
   return (long long)(((unsigned long long)hi << 32) | lo);
 }
 
-__device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned cidx, double t_s,
-                                double t_end, Acc& acc) {
+__device__ void run_region_warp(const KParams& p, const Lat& lt, int r, int n_iter, unsigned cidx,
+                                double t_s, double t_end, Acc& acc) {
   const int lane = threadIdx.x & 31;
   const int W = p.W, H = p.H;
   const size_t nr = (size_t)p.NR;
   const size_t cap = (size_t)p.cap;
   const int wp = n_iter & 1, rp = wp ^ 1;
-  const int rx = r % p.NX, ry = r / p.NX;
-  const bool spx = p.spans_x != 0, spy = p.spans_y != 0;
+  const int rx = lt.loc % lt.NX, ry = lt.loc / lt.NX;
+  const bool spx = lt.spans_x, spy = lt.spans_y;
   const uint32_t wmask = (W == 32) ? 0xFFFFFFFFu : ((1u << W) - 1u);
   const bool vlane = lane < H;
   const bool has_y = !spy, has_x = !spx;
@@ -845,10 +894,10 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
 
   // lane d < 4 serves direction d (0 N, 1 S, 2 W, 3 E)
   int qd = 0;
-  if (lane == 0) qd = ((ry + p.NY - 1) % p.NY) * p.NX + rx;
-  else if (lane == 1) qd = ((ry + 1) % p.NY) * p.NX + rx;
-  else if (lane == 2) qd = ry * p.NX + (rx + p.NX - 1) % p.NX;
-  else if (lane == 3) qd = ry * p.NX + (rx + 1) % p.NX;
+  if (lane == 0) qd = lt.off + ((ry + lt.NY - 1) % lt.NY) * lt.NX + rx;
+  else if (lane == 1) qd = lt.off + ((ry + 1) % lt.NY) * lt.NX + rx;
+  else if (lane == 2) qd = lt.off + ry * lt.NX + (rx + lt.NX - 1) % lt.NX;
+  else if (lane == 3) qd = lt.off + ry * lt.NX + (rx + 1) % lt.NX;
   const bool hasd = (lane < 2 && has_y) || (lane >= 2 && lane < 4 && has_x);
 
   // ---- skip when no neighbour's lists changed in the last iteration
@@ -919,7 +968,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
     const uint32_t e = vlane ? (eq_count(s0, s1, s2, k % 5) & (k >= 5 ? row : ~row) & wmask) : 0u;
     const unsigned tot = __reduce_add_sync(kFull, (unsigned)__popc(e));
     if (lane == k) myN = tot;
-    lam += (unsigned long long)tot * p.P[k];
+    lam += (unsigned long long)tot * lt.P[k];
   }
   int mag0 = 0, bond0 = 0;
   {
@@ -937,7 +986,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
   const int ein = (lane == 0) ? 1 : (lane == 1) ? 0 : (lane == 2) ? 3 : 2;
   unsigned len = 0, idx = 0, npos = 0, npos2 = 0;
   double nt = INF, nt2 = INF;
-  if (hasd) {
+  if (hasd && n_iter >= 2) {     // iteration 1: the canonical assumption (§5)
     len = __ldcg(&p.hl[((size_t)rp * 4 + ein) * nr + qd]);
     if (len > 0) {
       const size_t a = (((size_t)rp * 4 + ein) * cap) * nr + qd;
@@ -985,7 +1034,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
       const unsigned long long plo = mV * lam, phi = __umul64hi(mV, lam);
       const unsigned long long q53 = (phi << 11) | (plo >> 53);
       const bool exact = (plo & ((1ull << 53) - 1ull)) == 0ull;
-      const unsigned long long term = (lane < 10) ? (unsigned long long)myN * p.P[lane < 10 ? lane : 0] : 0ull;
+      const unsigned long long term = (lane < 10) ? (unsigned long long)myN * lt.P[lane < 10 ? lane : 0] : 0ull;
       unsigned long long A = term;
 #pragma unroll
       for (int d = 1; d < 16; d <<= 1) {
@@ -996,9 +1045,9 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
       const int ks = __ffs(__ballot_sync(kFull, hit)) - 1;
       const unsigned long long Aprev = shfl_u64(A - term, ks);
       const unsigned Nks = __shfl_sync(kFull, myN, ks);
-      const unsigned long long Pk = p.P[ks];
+      const unsigned long long Pk = lt.P[ks];
       // position in the class (Eqs. 3.7-3.8): floor((V Lambda - A(k*-1)) / p_k*)
-      unsigned long long jl = class_pos(q53 - Aprev, Pk, p.Rp[ks]);
+      unsigned long long jl = class_pos(q53 - Aprev, Pk, lt.Rp[ks]);
       if (jl >= Nks) jl = Nks - 1;
       const unsigned j = (unsigned)jl;
       // the j-th class-k* site in row-major order
@@ -1051,7 +1100,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
         if (!(code & 0x10u)) return;
         const int from = (int)(code & 0xFu), to = from + delta;
         dN += (lane == to) - (lane == from);
-        dlam += (long long)(p.P[to] - p.P[from]);
+        dlam += (long long)(lt.P[to] - lt.P[from]);
       };
       apply(m_mid & 0x1Fu, s_old ? -5 : 5);
       apply((m_mid >> 5) & 0x1Fu, dnb);
@@ -1117,7 +1166,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
       if (boundary) ++bevents;
       if (lane == 0 && p.tcap > 0 && i < (unsigned long long)p.tcap) {
         p.trt[(size_t)r * p.tcap + i] = tau;
-        p.trs[(size_t)r * p.tcap + i] = (gy0 + fy) * (uint32_t)p.L + gx0 + fx;
+        p.trs[(size_t)r * p.tcap + i] = (gy0 + fy) * (uint32_t)lt.L + gx0 + fx;
       }
       ++events;
       if (overflow) break;
@@ -1129,7 +1178,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
         x = px;
         kv = pkv;
       } else {
-        draw_event(i, (uint32_t)r, p.key0, p.key1, x, kv);
+        draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
       }
       pvalid = (i + 1ull) < hi_ring;
       if (pvalid) {
@@ -1156,7 +1205,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
       const int cnew = __shfl_sync(kFull, cnew_l, uy);
       const int cold = cnew + (up_now ? -1 : 1);
       myN = (unsigned)((int)myN + (lane == cnew) - (lane == cold));
-      lam = lam - p.P[cold] + p.P[cnew];
+      lam = lam - lt.P[cold] + lt.P[cnew];
       if (lane == who) {                     // advance the cursor
         ++idx;
         nt = nt2;
@@ -1181,7 +1230,7 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
     if (!((e < 2) ? has_y : has_x)) continue;
     const unsigned nn = (e == 0) ? olen0 : (e == 1) ? olen1 : (e == 2) ? olen2 : olen3;
     const unsigned n_new = nn < (unsigned)cap ? nn : (unsigned)cap;
-    const unsigned n_old = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
+    const unsigned n_old = n_iter >= 2 ? __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]) : 0u;
     bool diff = n_new != n_old;
     const unsigned n_min = n_new < n_old ? n_new : n_old;
     for (unsigned j = lane; j < n_min; j += 32) {
@@ -1222,21 +1271,21 @@ __device__ void run_region_warp(const KParams& p, int r, int n_iter, unsigned ci
   }
 }
 
-// Halo words of region r from the committed rows of its four neighbours.
-__device__ void compute_halo(const KParams& p, int r, unsigned cidx) {
+// Halo words of region r from copy `cidx` of the rows of its four neighbours.
+__device__ void compute_halo(const KParams& p, const Lat& lt, int r, unsigned cidx) {
   const size_t nr = (size_t)p.NR;
-  const int rx = r % p.NX, ry = r / p.NX;
+  const int rx = lt.loc % lt.NX, ry = lt.loc / lt.NX;
   const uint32_t* rows_c = p.rows + (size_t)cidx * p.H * nr;
   uint32_t hN = 0, hS = 0, hW = 0, hE = 0;
-  if (!p.spans_y) {
-    const int qN = ((ry + p.NY - 1) % p.NY) * p.NX + rx;
-    const int qS = ((ry + 1) % p.NY) * p.NX + rx;
+  if (!lt.spans_y) {
+    const int qN = lt.off + ((ry + lt.NY - 1) % lt.NY) * lt.NX + rx;
+    const int qS = lt.off + ((ry + 1) % lt.NY) * lt.NX + rx;
     hN = __ldcg(&rows_c[(size_t)(p.H - 1) * nr + qN]);
     hS = __ldcg(&rows_c[qS]);
   }
-  if (!p.spans_x) {
-    const int qW = ry * p.NX + (rx + p.NX - 1) % p.NX;
-    const int qE = ry * p.NX + (rx + 1) % p.NX;
+  if (!lt.spans_x) {
+    const int qW = lt.off + ry * lt.NX + (rx + lt.NX - 1) % lt.NX;
+    const int qE = lt.off + ry * lt.NX + (rx + 1) % lt.NX;
     for (int y = 0; y < p.H; ++y) {
       hW |= ((__ldcg(&rows_c[(size_t)y * nr + qW]) >> (p.W - 1)) & 1u) << y;
       hE |= (__ldcg(&rows_c[(size_t)y * nr + qE]) & 1u) << y;
@@ -1251,21 +1300,24 @@ __device__ void compute_halo(const KParams& p, int r, unsigned cidx) {
 // ---------------------------------------------------------------- persistent kernel
 // The DO(step) / DO(iteration) loops of the §4 procedure for nwin windows.
 // Ring top-up at a window start: the block's threads together draw the pairs of
-// events [max(rhi, i_c), i_c + K) for each region of the block.
-__device__ void fill_ring(const KParams& p, unsigned cidx) {
+// events [max(rhi, i_c), i_c + K) for each region of the block that has a
+// top-up pending (the regions of its slots: b*rl + l + k*gridDim.x*rl).
+__device__ void fill_ring(const KParams& p) {
   const size_t nr = (size_t)p.NR;
   const unsigned long long kmask = (unsigned long long)p.K - 1ull;
   const int lstride = gridDim.x * p.rl;
   for (int l = 0; l < p.rl; ++l) {
     for (int r = blockIdx.x * p.rl + l; r < p.NR; r += lstride) {
-      const unsigned long long lo = p.ci[cidx * nr + r];
+      if (!p.rfill[r]) continue;
+      const Lat lt = lat_of(p, r);
+      const unsigned long long lo = __ldcg(&p.ci[(size_t)p.rcidx[r] * nr + r]);
       const unsigned long long hi_old = p.rhi[r];
       const unsigned long long from = hi_old > lo ? hi_old : lo;
       const unsigned long long to = lo + (unsigned long long)p.K;
       for (unsigned long long i = from + threadIdx.x; i < to; i += blockDim.x) {
         double x;
         unsigned long long kv;
-        draw_event(i, (uint32_t)r, p.key0, p.key1, x, kv);
+        draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
         const size_t a = (size_t)(i & kmask) * nr + r;
         p.rx[a] = x;
         p.rkv[a] = kv;
@@ -1275,12 +1327,13 @@ __device__ void fill_ring(const KParams& p, unsigned cidx) {
   __syncthreads();
   for (int l = threadIdx.x; l < p.rl; l += blockDim.x)
     for (int r = blockIdx.x * p.rl + l; r < p.NR; r += lstride)
-      p.rhi[r] = p.ci[cidx * nr + r] + (unsigned long long)p.K;
+      if (p.rfill[r]) {
+        p.rhi[r] = __ldcg(&p.ci[(size_t)p.rcidx[r] * nr + r]) + (unsigned long long)p.K;
+        p.rfill[r] = 0;
+      }
+  __syncthreads();
 }
 
-// MODE 0: one lane per region (region lanes are the first rl threads of a
-// block); MODE 1: one warp per region (rl = warps per block).  Region slot j of
-// block b owns regions b*rl + j + k*(gridDim.x*rl).
 #ifndef SR_WARP_MIN_BLOCKS
 #define SR_WARP_MIN_BLOCKS 7
 #endif
@@ -1306,9 +1359,6 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
   const bool is_slot = (LANES ? lane < p.lanes : true) && slot < p.rl;
   const int sstride = gridDim.x * p.rl;
   const int sfirst = is_slot ? (int)(blockIdx.x * p.rl + slot) : p.NR;
-  // plain per-thread striding for the simple phases
-  const int tfirst = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int tstride = (int)(gridDim.x * blockDim.x);
   Region g;
   const int stride = p.rl;
   g.rows = smem + (LANES && is_slot ? slot : 0);
@@ -1318,14 +1368,9 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
   g.stride = stride;
   g.W = p.W;
   g.H = p.H;
-  g.spans_x = p.spans_x != 0;
-  g.spans_y = p.spans_y != 0;
   g.wmask = (p.W == 32) ? 0xFFFFFFFFu : ((1u << p.W) - 1u);
   DevStats* st = p.st;
   const size_t nr = (size_t)p.NR;
-  unsigned cidx = *(volatile unsigned*)&st->cidx;
-  unsigned giter = 0;
-  double t_s = p.t0;
   const bool reporter = LANES ? true : (threadIdx.x & 31) == 0;
   unsigned long long run_cyc = 0ull;
   // per-slot busy cycles, reported when the launch ends normally
@@ -1342,129 +1387,186 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
     }
   } report{st, &run_cyc, reporter && is_slot};
 
-  for (int w = 0; w < p.nwin; ++w) {
-    const double t_end = __dadd_rn(t_s, p.Tw);
-    // canonical assumption (§5): no neighbour flips -> empty previous lists
-    for (int r = tfirst; r < p.NR; r += tstride)
-      for (int e = 0; e < 4; ++e) p.hl[(size_t)e * nr + r] = 0u;   // parity 0
-    fill_ring(p, cidx);
-    if (!grid_barrier(st, p.timeout_cycles)) return;
+  // ---- launch start: every region begins iteration 1 of its lattice's first window
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned active = 0;
+    for (int b = 0; b < p.nrep; ++b) active += p.reps[b].nwin > 0 ? 1u : 0u;
+    st->active = active;
+  }
+  if (blockIdx.x == 0)
+    for (int b = threadIdx.x; b < p.nrep; b += blockDim.x) p.rs[b].windows_done = 0u;
+  if (is_slot && (LANES || (threadIdx.x & 31) == 0)) {
+    for (int r = sfirst; r < p.NR; r += sstride) {
+      const RepDesc* d = p.reps + __ldg(&p.rrep[r]);
+      p.rn[r] = 1u;
+      p.rwin[r] = 0u;
+      p.rts[r] = d->t0;
+      p.rfill[r] = d->nwin > 0 ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  fill_ring(p);
 
-    int n = 1;
-    bool converged = false;
-    for (; n <= p.max_iters; ++n) {
-      const unsigned fslot = giter % 3u;
-      ++giter;
-      Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, false, false};
-      const long long c0 = clock64();
-      for (int r = sfirst; r < p.NR; r += sstride) {
-        if (MODE == 0)
-          run_region<0>(p, r, n, cidx, t_s, t_end, g, acc);
-        else if (MODE == 2)
-          run_region<1>(p, r, n, cidx, t_s, t_end, g, acc);
-        else
-          run_region_warp(p, r, n, cidx, t_s, t_end, acc);
-      }
-      run_cyc += (unsigned long long)(clock64() - c0);
+  // ---- the DO(step) / DO(iteration) loops of the §4 procedure, every lattice
+  // of the launch in lockstep: one grid-wide synchronize per iteration, after
+  // which each region reads its own lattice's "no difference" flag and either
+  // iterates again or commits and starts its next window
+  unsigned giter = 0;
+  for (;;) {
+    const unsigned fslot = giter % 3u;
+    ++giter;
+    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, false, false};
+    const long long c0 = clock64();
+    for (int r = sfirst; r < p.NR; r += sstride) {
+      const int b = (int)__ldg(&p.rrep[r]);
+      const RepDesc* d = p.reps + b;
+      if (p.rwin[r] >= (unsigned)d->nwin) continue;
+      const Lat lt = lat_of(p, r);
+      const double t_s = p.rts[r];
+      const double t_end = __dadd_rn(t_s, d->Tw);
+      const unsigned cidx = p.rcidx[r];
+      const int n = (int)p.rn[r];
+      Acc ra = {0ull, 0ull, 0ull, 0ull, 0u, 0u, false, false};
+      if (MODE == 0)
+        run_region<0>(p, lt, r, n, cidx, t_s, t_end, g, ra);
+      else if (MODE == 2)
+        run_region<1>(p, lt, r, n, cidx, t_s, t_end, g, ra);
+      else
+        run_region_warp(p, lt, r, n, cidx, t_s, t_end, ra);
       if (reporter) {
-        if (acc.changed) atomicOr(&st->flags[fslot], 1u);
-        if (acc.overflow) atomicOr(&st->status, ST_CAPACITY);
-        if (acc.events) atomicAdd(&st->generated, acc.events);
-        if (acc.breaks) atomicAdd(&st->breaks, acc.breaks);
-        if (acc.fmax) atomicMax(&st->max_f, acc.fmax);
-        if (acc.emax) atomicMax(&st->max_win_events, acc.emax);
-        if (acc.passes) atomicAdd(&st->region_passes, acc.passes);
-        if (acc.skips) atomicAdd(&st->region_skips, acc.skips);
-      }
-      if (!grid_barrier(st, p.timeout_cycles)) return;
-      if (blockIdx.x == 0 && threadIdx.x == 0) st->flags[(fslot + 2u) % 3u] = 0u;
-      if (*(volatile unsigned*)&st->status & ST_CAPACITY) return;   // window not committed
-      if (*(volatile unsigned*)&st->flags[fslot] == 0u) {
-        converged = true;
-        break;
+        RepStats* rs = p.rs + b;
+        if (ra.changed) atomicOr(&p.rflags[fslot * p.nrep + b], 1u);
+        if (ra.overflow) atomicOr(&st->status, ST_CAPACITY);
+        if (ra.events) atomicAdd(&rs->generated, ra.events);
+        if (ra.breaks) atomicAdd(&rs->breaks, ra.breaks);
+        if (ra.fmax) atomicMax(&rs->max_f, ra.fmax);
+        if (ra.emax) atomicMax(&rs->max_win_events, ra.emax);
+        acc.passes += ra.passes;
+        acc.skips += ra.skips;
       }
     }
-    if (!converged) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&st->status, ST_NOT_CONVERGED);
-      return;
-    }
-    // ---- commit (statement 3 of §4: increment committed time by T_max)
-    unsigned long long committed = 0;
-    for (int r = tfirst; r < p.NR; r += tstride)
-      committed += __ldcg(&p.ci[(cidx ^ 1u) * nr + r]) - __ldcg(&p.ci[cidx * nr + r]);
-    if (committed) atomicAdd(&st->committed, committed);
-    cidx ^= 1u;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st->cidx = cidx;
-      st->windows += 1ull;
-      st->iterations += (unsigned long long)n;
-      st->last_iters = (unsigned)n;
-      if ((unsigned)n > st->max_iters_seen) st->max_iters_seen = (unsigned)n;
-      p.win_iters[w % kWinRing] = (unsigned)n;
-      st->windows_done = (unsigned)(w + 1);
+    run_cyc += (unsigned long long)(clock64() - c0);
+    if (reporter) {
+      if (acc.passes) atomicAdd(&st->region_passes, acc.passes);
+      if (acc.skips) atomicAdd(&st->region_skips, acc.skips);
     }
     if (!grid_barrier(st, p.timeout_cycles)) return;
-    for (int r = tfirst; r < p.NR; r += tstride) compute_halo(p, r, cidx);
-    if (!grid_barrier(st, p.timeout_cycles)) return;
-    t_s = t_end;
+    if (*(volatile unsigned*)&st->status & (ST_CAPACITY | ST_NOT_CONVERGED)) return;
+    if (*(volatile unsigned*)&st->active == 0u) return;     // every lattice is done
+    // the flag slot of the next-but-one iteration starts clear
+    for (int b = (int)(blockIdx.x * blockDim.x + threadIdx.x); b < p.nrep; b += gridDim.x * blockDim.x)
+      p.rflags[((fslot + 2u) % 3u) * p.nrep + b] = 0u;
+
+    // ---- per region: commit or iterate again (statement 3 of §4)
+    if (is_slot && (LANES || (threadIdx.x & 31) == 0)) {
+      for (int r = sfirst; r < p.NR; r += sstride) {
+        const int b = (int)__ldg(&p.rrep[r]);
+        const RepDesc* d = p.reps + b;
+        const unsigned w = p.rwin[r];
+        if (w >= (unsigned)d->nwin) continue;
+        RepStats* rs = p.rs + b;
+        const unsigned n = p.rn[r];
+        if (*(volatile unsigned*)&p.rflags[fslot * p.nrep + b] == 0u) {
+          // no region of this lattice changed its lists: its histories are the
+          // fixed point; the tentative state becomes the committed one
+          const unsigned cnew = p.rcidx[r] ^ 1u;
+          const unsigned long long dc = __ldcg(&p.ci[(size_t)cnew * nr + r]) -
+                                        __ldcg(&p.ci[(size_t)(cnew ^ 1u) * nr + r]);
+          if (dc) atomicAdd(&rs->committed, dc);
+          p.rcidx[r] = (uint8_t)cnew;
+          const Lat lt = lat_of(p, r);
+          compute_halo(p, lt, r, cnew);     // neighbours commit in this same step
+          p.rts[r] = __dadd_rn(p.rts[r], d->Tw);
+          p.rwin[r] = w + 1u;
+          p.rn[r] = 1u;
+          p.rfill[r] = (w + 1u < (unsigned)d->nwin) ? 1 : 0;
+          if (lt.loc == 0) {
+            rs->windows += 1ull;
+            rs->iterations += (unsigned long long)n;
+            rs->last_iters = n;
+            if (n > rs->max_iters_seen) rs->max_iters_seen = n;
+            rs->windows_done = w + 1u;
+            if (b == 0) p.win_iters[w % kWinRing] = n;
+            if (w + 1u == (unsigned)d->nwin) atomicSub(&st->active, 1u);
+          }
+        } else if ((int)n >= p.max_iters) {
+          atomicOr(&st->status, ST_NOT_CONVERGED);
+        } else {
+          p.rn[r] = n + 1u;
+        }
+      }
+    }
+    __syncthreads();
+    fill_ring(p);
   }
 }
 
 // ---------------------------------------------------------------- helpers
-__global__ void halo_kernel(KParams p, unsigned cidx) {
+__global__ void halo_kernel(KParams p) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < p.NR) compute_halo(p, r, cidx);
+  if (r < p.NR) compute_halo(p, lat_of(p, r), r, p.rcidx[r]);
 }
 
-// Fair coin / all up / all down rows (copy 0).
-__global__ void init_rows_kernel(KParams p, int mode) {
+// Rows (copy 0) of every region of lattice `rep` (of every lattice when
+// rep < 0) from the lattice's init mode: fair coin / all up / all down.
+__global__ void init_rows_kernel(KParams p, int rep) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)p.NR * p.H) return;
   const int r = (int)(t % p.NR), y = (int)(t / p.NR);
-  const int rx = r % p.NX, ry = r / p.NX;
+  const Lat lt = lat_of(p, r);
+  if (rep >= 0 && lt.rep != rep) return;
+  const int mode = p.reps[lt.rep].init_mode;
+  const int rx = lt.loc % lt.NX, ry = lt.loc / lt.NX;
   uint32_t word = 0;
   if (mode == SR_INIT_ALL_UP) {
     word = (p.W == 32) ? 0xFFFFFFFFu : ((1u << p.W) - 1u);
   } else if (mode == SR_INIT_FAIR_COIN) {
     const uint32_t gy = (uint32_t)(ry * p.H + y);
     for (int x = 0; x < p.W; ++x) {
-      const uint32_t site = gy * (uint32_t)p.L + (uint32_t)(rx * p.W + x);
+      const uint32_t site = gy * (uint32_t)lt.L + (uint32_t)(rx * p.W + x);
       uint32_t w[4];
-      philox4x32_10(site, 0u, 0u, 1u, p.key0, p.key1, w);
+      philox4x32_10(site, 0u, 0u, 1u, lt.key0, lt.key1, w);
       word |= (w[0] & 1u) << x;
     }
   }
   p.rows[(size_t)y * p.NR + r] = word;
 }
 
-// Rows (copy 0) from an int8 lattice in device memory.
-__global__ void pack_rows_kernel(KParams p, const int8_t* spins) {
+// Rows (copy 0) of lattice b from an int8 L x L array in device memory.
+__global__ void pack_rows_kernel(KParams p, int b, const int8_t* spins) {
+  const RepDesc& d = p.reps[b];
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)p.NR * p.H) return;
-  const int r = (int)(t % p.NR), y = (int)(t / p.NR);
-  const int rx = r % p.NX, ry = r / p.NX;
-  const size_t base = (size_t)(ry * p.H + y) * p.L + (size_t)rx * p.W;
+  if (t >= (size_t)d.NR * p.H) return;
+  const int loc = (int)(t % d.NR), y = (int)(t / d.NR);
+  const int r = d.off + loc;
+  const int rx = loc % d.NX, ry = loc / d.NX;
+  const size_t base = (size_t)(ry * p.H + y) * d.L + (size_t)rx * p.W;
   uint32_t word = 0;
   for (int x = 0; x < p.W; ++x) word |= (uint32_t)(spins[base + x] > 0) << x;
   p.rows[(size_t)y * p.NR + r] = word;
 }
 
-__global__ void unpack_rows_kernel(KParams p, unsigned cidx, int8_t* spins) {
+// Committed spins of lattice b as an int8 L x L array.
+__global__ void unpack_rows_kernel(KParams p, int b, int8_t* spins) {
+  const RepDesc& d = p.reps[b];
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)p.L * p.L) return;
-  const int gx = (int)(t % p.L), gy = (int)(t / p.L);
-  const int r = (gy / p.H) * p.NX + gx / p.W;
-  const uint32_t word = p.rows[((size_t)cidx * p.H + gy % p.H) * p.NR + r];
+  if (t >= (size_t)d.L * d.L) return;
+  const int gx = (int)(t % d.L), gy = (int)(t / d.L);
+  const int r = d.off + (gy / p.H) * d.NX + gx / p.W;
+  const uint32_t word = p.rows[((size_t)p.rcidx[r] * p.H + gy % p.H) * p.NR + r];
   spins[t] = ((word >> (gx % p.W)) & 1u) ? 1 : -1;
 }
 
-// Clock state at t = 0: tau_0 = 0, first pair (U_1, V_1) of every region.
-__global__ void init_carry_kernel(KParams p) {
+// Clock state at t = 0 of every region of lattice `rep` (every lattice when
+// rep < 0): tau_0 = 0, first pair (U_1, V_1), committed copy 0, empty ring.
+__global__ void init_carry_kernel(KParams p, int rep) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= p.NR) return;
+  const Lat lt = lat_of(p, r);
+  if (rep >= 0 && lt.rep != rep) return;
   double x;
   unsigned long long kv;
-  draw_event(0ull, (uint32_t)r, p.key0, p.key1, x, kv);
+  draw_event(0ull, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
   p.ci[r] = 0ull;
   p.cx[r] = x;
   p.ckv[r] = kv;
@@ -1472,23 +1574,26 @@ __global__ void init_carry_kernel(KParams p) {
   p.ct[r] = 0.0;
   p.cim[r] = 0.0;
   p.cib[r] = 0.0;
-  p.rhi[r] = 0ull;   // ring empty
+  p.rhi[r] = 0ull;    // ring empty
+  p.rcidx[r] = 0;
 }
 
-// Spin sum and owned-bond sum (right and down bonds of every site), exact.
-__global__ void observe_ints_kernel(KParams p, unsigned cidx, long long* out2) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// Spin sum and owned-bond sum (right and down bonds of every site) of lattice b, exact.
+__global__ void observe_ints_kernel(KParams p, int b, long long* out2) {
+  const RepDesc& d = p.reps[b];
+  const int loc = blockIdx.x * blockDim.x + threadIdx.x;
   long long mag = 0, bonds = 0;
-  if (r < p.NR) {
+  if (loc < d.NR) {
+    const int r = d.off + loc;
     const size_t nr = (size_t)p.NR;
     const uint32_t wmask = (p.W == 32) ? 0xFFFFFFFFu : ((1u << p.W) - 1u);
-    const uint32_t* rows_c = p.rows + (size_t)cidx * p.H * nr;
+    const uint32_t* rows_c = p.rows + (size_t)p.rcidx[r] * p.H * nr;
     const uint32_t hS = p.halo[1 * nr + r], hE = p.halo[3 * nr + r];
     for (int y = 0; y < p.H; ++y) {
       const uint32_t rw = rows_c[(size_t)y * nr + r];
       const uint32_t dn = (y < p.H - 1) ? rows_c[(size_t)(y + 1) * nr + r]
-                                        : (p.spans_y ? rows_c[r] : hS);
-      const uint32_t rbit = p.spans_x ? (rw & 1u) : (hE >> y) & 1u;
+                                        : (d.spans_y ? rows_c[r] : hS);
+      const uint32_t rbit = d.spans_x ? (rw & 1u) : (hE >> y) & 1u;
       const uint32_t rt = (rw >> 1) | (rbit << (p.W - 1));
       mag += 2 * __popc(rw) - p.W;
       bonds += (p.W - 2 * __popc((rw ^ rt) & wmask)) + (p.W - 2 * __popc((rw ^ dn) & wmask));
@@ -1504,22 +1609,25 @@ __global__ void observe_ints_kernel(KParams p, unsigned cidx, long long* out2) {
   }
 }
 
-// Fixed-order FP64 sums of the per-region time integrals (one block).
-__global__ void observe_integrals_kernel(KParams p, unsigned cidx, double* out2) {
+// Fixed-order FP64 sums of the per-region time integrals of lattice b (one block).
+__global__ void observe_integrals_kernel(KParams p, int b, double* out2) {
   __shared__ double sm[2][1024];
+  const RepDesc& d = p.reps[b];
   const size_t nr = (size_t)p.NR;
   double a = 0.0, c = 0.0;
-  for (size_t r = threadIdx.x; r < nr; r += blockDim.x) {
-    a = __dadd_rn(a, p.cim[cidx * nr + r]);
-    c = __dadd_rn(c, p.cib[cidx * nr + r]);
+  for (int loc = threadIdx.x; loc < d.NR; loc += blockDim.x) {
+    const int r = d.off + loc;
+    const size_t ci = (size_t)p.rcidx[r];
+    a = __dadd_rn(a, p.cim[ci * nr + r]);
+    c = __dadd_rn(c, p.cib[ci * nr + r]);
   }
   sm[0][threadIdx.x] = a;
   sm[1][threadIdx.x] = c;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      sm[0][threadIdx.x] = __dadd_rn(sm[0][threadIdx.x], sm[0][threadIdx.x + s]);
-      sm[1][threadIdx.x] = __dadd_rn(sm[1][threadIdx.x], sm[1][threadIdx.x + s]);
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) {
+      sm[0][threadIdx.x] = __dadd_rn(sm[0][threadIdx.x], sm[0][threadIdx.x + k]);
+      sm[1][threadIdx.x] = __dadd_rn(sm[1][threadIdx.x], sm[1][threadIdx.x + k]);
     }
     __syncthreads();
   }
@@ -1527,6 +1635,21 @@ __global__ void observe_integrals_kernel(KParams p, unsigned cidx, double* out2)
     out2[0] = sm[0][0];
     out2[1] = sm[1][0];
   }
+}
+
+// Committed clock state of lattice b (per region: index, x, b, t_last), and
+// the committed copy of every region's event index.
+__global__ void gather_carry_kernel(KParams p, int b, unsigned long long* i_out, double* x_out,
+                                    double* b_out, double* t_out) {
+  const RepDesc& d = p.reps[b];
+  const int loc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= d.NR) return;
+  const int r = d.off + loc;
+  const size_t c = (size_t)p.rcidx[r] * p.NR + r;
+  if (i_out) i_out[loc] = p.ci[c];
+  if (x_out) x_out[loc] = p.cx[c];
+  if (b_out) b_out[loc] = p.cb[c];
+  if (t_out) t_out[loc] = p.ct[c];
 }
 
 __global__ void eval_draws_kernel(uint32_t key0, uint32_t key1, uint32_t region,
@@ -1563,14 +1686,24 @@ __global__ void eval_softfloat_kernel(int op, const double* a, const double* b, 
 using namespace sr;
 
 struct sr_ctx {
-  sr_params prm;
-  int NX, NY, NR, F;
-  unsigned long long P[10];
+  sr_params prm;                // common settings (the region shape, capacities, launch)
+  int nrep;                     // lattices
+  sr_replica* reps;             // [nrep] their parameters
+  RepDesc* hdesc;               // [nrep] host copy of the descriptors
+  double* t_c;                  // [nrep] committed time of each lattice
+  int NR, F, Lmax;
   double scale;
   cudaStream_t stream;
   bool own_stream;
   int num_sms;
   int clock_khz;
+  // device state
+  RepDesc* desc;
+  RepStats* rs;
+  uint32_t *rrep, *rflags;
+  uint8_t *rcidx, *rfill;
+  uint32_t *rn, *rwin;
+  double* rts;
   uint32_t *rows, *halo, *hl, *trs, *win_iters, *log, *loghdr;
   uint8_t* chg;
   int CB;
@@ -1583,12 +1716,12 @@ struct sr_ctx {
   bool cap_auto;
   DevStats* st;
   DevStats* h_st;
+  RepStats* h_rs;
   long long* obs_i;
   double* obs_f;
   long long* h_obs_i;
   double* h_obs_f;
   int8_t* stage;
-  double t_c;
   int rl, tpb, blocks, mode, lanes;
   size_t smem;
   int last_nwin;
@@ -1607,7 +1740,7 @@ int bitlen(long long v) {
 
 // p_k for the ten classes k = 5*[s=+1] + n_up (Eqs. 2.2-2.3), then the
 // fixed-point grid P_k = round(p_k 2^F), F = 63 - bitlen(sites per region).
-void rate_table(const sr_params& p, int F, unsigned long long P[10]) {
+void rate_table(const sr_replica& p, int F, unsigned long long P[10]) {
   for (int k = 0; k < 10; ++k) {
     const int s = (k >= 5) ? 1 : -1;
     const int n_up = k % 5;
@@ -1626,22 +1759,21 @@ void rate_table(const sr_params& p, int F, unsigned long long P[10]) {
 KParams make_params(const sr_ctx* c) {
   KParams k;
   std::memset(&k, 0, sizeof k);
-  k.L = c->prm.L;
   k.W = c->prm.region_w;
   k.H = c->prm.region_h;
-  k.NX = c->NX;
-  k.NY = c->NY;
   k.NR = c->NR;
-  k.spans_x = c->NX == 1;
-  k.spans_y = c->NY == 1;
-  for (int i = 0; i < 10; ++i) {
-    k.P[i] = c->P[i];
-    k.Rp[i] = c->P[i] ? ~0ull / c->P[i] : 0ull;
-  }
+  k.nrep = c->nrep;
+  k.reps = c->desc;
+  k.rrep = c->rrep;
+  k.rs = c->rs;
+  k.rflags = c->rflags;
+  k.rcidx = c->rcidx;
+  k.rn = c->rn;
+  k.rwin = c->rwin;
+  k.rts = c->rts;
+  k.rfill = c->rfill;
   k.scale = c->scale;
   k.F = c->F;
-  k.key0 = (uint32_t)c->prm.seed;
-  k.key1 = (uint32_t)(c->prm.seed >> 32);
   k.rows = c->rows;
   k.halo = c->halo;
   k.ci = c->ci;
@@ -1708,30 +1840,53 @@ bool allow_smem(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
-// Initial state: rows (copy 0) come from the caller or the init kernel.
-int init_state(sr_ctx* c, const int8_t* dev_spins) {
+int upload_desc(sr_ctx* c) {
+  return cuda_rc(cudaMemcpyAsync(c->desc, c->hdesc, (size_t)c->nrep * sizeof(RepDesc),
+                                 cudaMemcpyHostToDevice, c->stream));
+}
+
+// Initial state of lattice `rep` (every lattice when rep < 0): rows (copy 0)
+// from dev_spins (one lattice) or the lattice's init mode, clocks at t = 0,
+// counters cleared; then the halos of every region.
+int init_state(sr_ctx* c, int rep, const int8_t* dev_spins) {
   KParams k = make_params(c);
-  const size_t nrow = (size_t)c->NR * c->prm.region_h;
-  const unsigned gb = (unsigned)((nrow + 255) / 256);
-  if (dev_spins)
-    pack_rows_kernel<<<gb, 256, 0, c->stream>>>(k, dev_spins);
-  else
-    init_rows_kernel<<<gb, 256, 0, c->stream>>>(k, c->prm.init_mode);
-  halo_kernel<<<(c->NR + 255) / 256, 256, 0, c->stream>>>(k, 0u);
-  init_carry_kernel<<<(c->NR + 255) / 256, 256, 0, c->stream>>>(k);
+  int rc = upload_desc(c);
+  if (rc != SR_OK) return rc;
+  const unsigned gr = (unsigned)((c->NR + 255) / 256);
+  init_carry_kernel<<<gr, 256, 0, c->stream>>>(k, rep);
+  if (dev_spins) {
+    const RepDesc& d = c->hdesc[rep];
+    pack_rows_kernel<<<(unsigned)(((size_t)d.NR * k.H + 255) / 256), 256, 0, c->stream>>>(k, rep,
+                                                                                          dev_spins);
+  } else {
+    init_rows_kernel<<<(unsigned)(((size_t)c->NR * k.H + 255) / 256), 256, 0, c->stream>>>(k, rep);
+  }
+  halo_kernel<<<gr, 256, 0, c->stream>>>(k);
   c->launches += 3;
-  if (cudaMemsetAsync(c->st, 0, sizeof(DevStats), c->stream) != cudaSuccess) return SR_ECUDA;
-  c->t_c = 0.0;
+  for (int b = 0; b < c->nrep; ++b) {
+    if (rep >= 0 && b != rep) continue;
+    if (cudaMemsetAsync(c->rs + b, 0, sizeof(RepStats), c->stream) != cudaSuccess) return SR_ECUDA;
+    c->t_c[b] = 0.0;
+  }
+  if (rep < 0 && cudaMemsetAsync(c->st, 0, sizeof(DevStats), c->stream) != cudaSuccess) return SR_ECUDA;
   c->last_nwin = 0;
   return cuda_rc(cudaGetLastError());
 }
 
-int launch_relax(sr_ctx* c, double t0, double Tw, int nwin) {
+// One persistent launch running, for each lattice b, nwin[b] windows of
+// length Tw[b] from its committed time.
+int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
+  for (int b = 0; b < c->nrep; ++b) {
+    c->hdesc[b].t0 = c->t_c[b];
+    c->hdesc[b].Tw = Tw[b];
+    c->hdesc[b].nwin = nwin[b];
+  }
+  int rc = upload_desc(c);
+  if (rc != SR_OK) return rc;
   KParams k = make_params(c);
-  k.t0 = t0;
-  k.Tw = Tw;
-  k.nwin = nwin;
-  if (cudaMemsetAsync(c->st, 0, offsetof(DevStats, cidx), c->stream) != cudaSuccess) return SR_ECUDA;
+  if (cudaMemsetAsync(c->st, 0, offsetof(DevStats, region_passes), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->rflags, 0, 3 * (size_t)c->nrep * sizeof(uint32_t), c->stream) != cudaSuccess)
+    return SR_ECUDA;
   void* args[] = {&k};
   const void* fn = c->mode == 1 ? (const void*)relax_kernel<1>
                                 : (c->mode == 2 ? (const void*)relax_kernel<2> : (const void*)relax_kernel<0>);
@@ -1743,7 +1898,9 @@ int launch_relax(sr_ctx* c, double t0, double Tw, int nwin) {
   }
   c->launches += 1;
   if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaMemcpyAsync(c->h_rs, c->rs, (size_t)c->nrep * sizeof(RepStats), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess)
     return SR_ECUDA;
   return cuda_rc(cudaStreamSynchronize(c->stream));
 }
@@ -1779,66 +1936,93 @@ int set_ring(sr_ctx* c, int K) {
 void free_all(sr_ctx* c) {
   void* dev[] = {c->rows, c->halo, c->hl, c->trs, c->win_iters, c->ci, c->ckv, c->cx, c->cb,
                  c->ct, c->cim, c->cib, c->ht, c->trt, c->hp, c->st, c->obs_i, c->obs_f, c->stage,
-                 c->rx, c->rkv, c->rhi, c->chg, c->log, c->loghdr};
+                 c->rx, c->rkv, c->rhi, c->chg, c->log, c->loghdr, c->desc, c->rs, c->rrep,
+                 c->rflags, c->rcidx, c->rfill, c->rn, c->rwin, c->rts};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (c->h_st) cudaFreeHost(c->h_st);
+  if (c->h_rs) cudaFreeHost(c->h_rs);
   if (c->h_obs_i) cudaFreeHost(c->h_obs_i);
   if (c->h_obs_f) cudaFreeHost(c->h_obs_f);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  std::free(c->reps);
+  std::free(c->hdesc);
+  std::free(c->t_c);
 }
 
-}  // namespace
-
-extern "C" {
-
-const char* sr_strerror(int code) {
-  switch (code) {
-    case SR_OK: return "ok";
-    case SR_EINVAL: return "invalid argument";
-    case SR_ENOMEM: return "out of memory";
-    case SR_ECUDA: return "CUDA error";
-    case SR_NOT_CONVERGED: return "relaxation did not converge within the iteration cap";
-    case SR_CAPACITY: return "boundary history exceeded the largest capacity";
-    case SR_TIMEOUT: return "grid-wide synchronize timed out";
-    case SR_EUNSUPPORTED: return "unsupported configuration";
-    case SR_ETOOLARGE: return "problem does not fit the fixed no-allocation scratch";
-    default: return "unknown status";
-  }
+int check_replica(const sr_replica& r, int W, int H) {
+  if (r.L < 3 || r.L % W || r.L % H) return SR_EINVAL;
+  if (!(r.T > 0.0) || !std::isfinite(r.J) || !std::isfinite(r.h) || std::isnan(r.T)) return SR_EINVAL;
+  if (r.init_mode < SR_INIT_FAIR_COIN || r.init_mode > SR_INIT_ALL_DOWN) return SR_EINVAL;
+  if (r.rates != SR_RATES_METROPOLIS && r.rates != SR_RATES_GLAUBER) return SR_EINVAL;
+  if ((long long)r.L * r.L > (1ll << 32)) return SR_EUNSUPPORTED;
+  return SR_OK;
 }
 
-int sr_create_ex(sr_ctx** out, const sr_params* prm) {
-  if (!out || !prm) return SR_EINVAL;
+// A context for n lattices sharing the region shape and settings of `p`.
+int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& p) {
   *out = nullptr;
-  const sr_params& p = *prm;
-  if (p.L < 3 || p.region_w < 1 || p.region_h < 1 || p.L % p.region_w || p.L % p.region_h)
-    return SR_EINVAL;
-  if (!(p.T > 0.0) || !std::isfinite(p.J) || !std::isfinite(p.h) || std::isnan(p.T)) return SR_EINVAL;
-  if (p.init_mode < SR_INIT_FAIR_COIN || p.init_mode > SR_INIT_ALL_DOWN) return SR_EINVAL;
-  if (p.rates != SR_RATES_METROPOLIS && p.rates != SR_RATES_GLAUBER) return SR_EINVAL;
+  if (n < 1 || !reps) return SR_EINVAL;
+  if (p.region_w < 1 || p.region_h < 1) return SR_EINVAL;
   if (p.capacity < 0 || p.max_iters < 0 || p.trace_capacity < 0 || p.threads_per_block < 0 ||
       p.block_threads < 0 || p.blocks < 0 || p.barrier_timeout_ms < 0)
     return SR_EINVAL;
+  if (p.lanes_per_region != 0 && p.lanes_per_region != 1 && p.lanes_per_region != 32) return SR_EINVAL;
+  if (p.lanes_per_warp < 0 || p.lanes_per_warp > 32 || p.time_arith < 0 || p.time_arith > 2)
+    return SR_EINVAL;
   if (p.region_w > 32 || p.region_h > 32) return SR_EUNSUPPORTED;
-  if ((long long)p.L * p.L > (1ll << 32)) return SR_EUNSUPPORTED;
-
+  for (int b = 0; b < n; ++b) {
+    const int rc = check_replica(reps[b], p.region_w, p.region_h);
+    if (rc != SR_OK) return rc;
+  }
   sr_ctx* c = (sr_ctx*)std::calloc(1, sizeof(sr_ctx));
   if (!c) return SR_ENOMEM;
   c->prm = p;
   if (c->prm.max_iters == 0) c->prm.max_iters = 1 << 16;
   if (c->prm.barrier_timeout_ms == 0) c->prm.barrier_timeout_ms = 2000;
-  c->NX = p.L / p.region_w;
-  c->NY = p.L / p.region_h;
-  c->NR = c->NX * c->NY;
-  c->F = 63 - bitlen((long long)p.region_w * p.region_h);
+  c->nrep = n;
+  c->reps = (sr_replica*)std::calloc((size_t)n, sizeof(sr_replica));
+  c->hdesc = (RepDesc*)std::calloc((size_t)n, sizeof(RepDesc));
+  c->t_c = (double*)std::calloc((size_t)n, sizeof(double));
+  if (!c->reps || !c->hdesc || !c->t_c) {
+    free_all(c);
+    std::free(c);
+    return SR_ENOMEM;
+  }
+  const int W = p.region_w, H = p.region_h;
+  c->F = 63 - bitlen((long long)W * H);
   c->scale = std::ldexp(1.0, -c->F);
-  rate_table(c->prm, c->F, c->P);
+  long long total = 0;
+  for (int b = 0; b < n; ++b) {
+    c->reps[b] = reps[b];
+    RepDesc& d = c->hdesc[b];
+    d.L = reps[b].L;
+    d.NX = d.L / W;
+    d.NY = d.L / H;
+    d.NR = d.NX * d.NY;
+    d.off = (int)total;
+    d.spans_x = d.NX == 1;
+    d.spans_y = d.NY == 1;
+    d.key0 = (uint32_t)reps[b].seed;
+    d.key1 = (uint32_t)(reps[b].seed >> 32);
+    d.init_mode = reps[b].init_mode;
+    rate_table(reps[b], c->F, d.P);
+    for (int k = 0; k < 10; ++k) d.Rp[k] = d.P[k] ? ~0ull / d.P[k] : 0ull;
+    total += d.NR;
+    if (d.L > c->Lmax) c->Lmax = d.L;
+  }
+  if (total > (1ll << 30)) {
+    free_all(c);
+    std::free(c);
+    return SR_EUNSUPPORTED;
+  }
+  c->NR = (int)total;
 
-  int rc = SR_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+    free_all(c);
     std::free(c);
     return SR_ECUDA;
   }
@@ -1846,26 +2030,17 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
     c->stream = (cudaStream_t)p.stream;
   } else {
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      free_all(c);
       std::free(c);
       return SR_ECUDA;
     }
     c->own_stream = true;
   }
 
-  // launch shape.  Warp per region while the regions fit the resident warps;
-  // otherwise one lane per region, with few region lanes per warp when the
-  // regions are few (less divergence, more warps to hide latency) and FP64
-  // time arithmetic while the FP64 pipe is not the limit.
-  const int H = p.region_h;
-  if (p.lanes_per_region != 0 && p.lanes_per_region != 1 && p.lanes_per_region != 32) {
-    std::free(c);
-    return SR_EINVAL;
-  }
-  if (p.lanes_per_warp < 0 || p.lanes_per_warp > 32 || p.time_arith < 0 || p.time_arith > 2) {
-    std::free(c);
-    return SR_EINVAL;
-  }
-  int rc_shape = SR_OK;
+  // launch shape: one warp per region on request; otherwise one lane per
+  // region, with few region lanes per warp when the regions are few (less
+  // divergence, more warps to hide latency), and FP64 time arithmetic while the
+  // FP64 pipe is not the limit
   if (p.lanes_per_region == 32) {
     c->mode = 1;
     int wpb = p.threads_per_block ? p.threads_per_block : 4;   // warps per block
@@ -1906,19 +2081,16 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, fn, c->tpb, c->smem) != cudaSuccess ||
         per_sm_blocks < 1) {
       cudaGetLastError();
-      rc_shape = SR_EUNSUPPORTED;
-    } else {
-      int blocks = p.blocks ? p.blocks : (c->NR + c->rl - 1) / c->rl;
-      if (blocks > per_sm_blocks * c->num_sms) blocks = per_sm_blocks * c->num_sms;
-      c->blocks = blocks;
+      free_all(c);
+      std::free(c);
+      return SR_EUNSUPPORTED;
     }
-  }
-  if (rc_shape != SR_OK) {
-    free_all(c);
-    std::free(c);
-    return rc_shape;
+    int blocks = p.blocks ? p.blocks : (c->NR + c->rl - 1) / c->rl;
+    if (blocks > per_sm_blocks * c->num_sms) blocks = per_sm_blocks * c->num_sms;
+    c->blocks = blocks;
   }
 
+  int rc = SR_OK;
   const size_t nr = (size_t)c->NR;
   rc |= dalloc(&c->rows, 2 * (size_t)H * nr);
   rc |= dalloc(&c->halo, 4 * nr);
@@ -1934,9 +2106,18 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   rc |= dalloc(&c->win_iters, kWinRing);
   rc |= dalloc(&c->obs_i, 2);
   rc |= dalloc(&c->obs_f, 2);
-  rc |= dalloc(&c->stage, (size_t)p.L * p.L);
+  rc |= dalloc(&c->stage, (size_t)c->Lmax * c->Lmax);
   rc |= dalloc(&c->rhi, nr);
   rc |= dalloc(&c->chg, 2 * nr);
+  rc |= dalloc(&c->desc, (size_t)n);
+  rc |= dalloc(&c->rs, (size_t)n);
+  rc |= dalloc(&c->rflags, 3 * (size_t)n);
+  rc |= dalloc(&c->rrep, nr);
+  rc |= dalloc(&c->rcidx, nr);
+  rc |= dalloc(&c->rfill, nr);
+  rc |= dalloc(&c->rn, nr);
+  rc |= dalloc(&c->rwin, nr);
+  rc |= dalloc(&c->rts, nr);
   // incremental replay log: lane mappings only
   c->CB = (c->mode == 1 || p.replay_records < 0) ? 0 : (p.replay_records ? p.replay_records : 64);
   if (c->CB > 0) {
@@ -1951,12 +2132,26 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   if (rc == SR_OK) rc = alloc_history(c, p.capacity ? p.capacity : 64);
   if (rc == SR_OK &&
       (cudaMallocHost((void**)&c->h_st, sizeof(DevStats)) != cudaSuccess ||
+       cudaMallocHost((void**)&c->h_rs, (size_t)n * sizeof(RepStats)) != cudaSuccess ||
        cudaMallocHost((void**)&c->h_obs_i, 2 * sizeof(long long)) != cudaSuccess ||
        cudaMallocHost((void**)&c->h_obs_f, 2 * sizeof(double)) != cudaSuccess))
     rc = SR_ENOMEM;
+  if (rc == SR_OK) {
+    uint32_t* map = (uint32_t*)std::malloc(nr * sizeof(uint32_t));
+    if (!map) {
+      rc = SR_ENOMEM;
+    } else {
+      for (int b = 0; b < n; ++b)
+        for (int j = 0; j < c->hdesc[b].NR; ++j) map[c->hdesc[b].off + j] = (uint32_t)b;
+      rc = cuda_rc(cudaMemcpyAsync(c->rrep, map, nr * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                   c->stream));
+      if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
+      std::free(map);
+    }
+  }
   if (rc == SR_OK && cudaMemsetAsync(c->hl, 0, 2 * 4 * nr * sizeof(uint32_t), c->stream) != cudaSuccess)
     rc = SR_ECUDA;
-  if (rc == SR_OK) rc = init_state(c, nullptr);
+  if (rc == SR_OK) rc = init_state(c, -1, nullptr);
   if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
   if (rc != SR_OK) {
     free_all(c);
@@ -1965,6 +2160,185 @@ int sr_create_ex(sr_ctx** out, const sr_params* prm) {
   }
   *out = c;
   return SR_OK;
+}
+
+// Run nwin[b] windows of length Tw[b] for every lattice b from its committed
+// time; capacity overflows grow the history and re-run what did not commit.
+int run_all(sr_ctx* c, const double* Tw, const int* nwin) {
+  for (int b = 0; b < c->nrep; ++b)
+    if (nwin[b] < 0 || (nwin[b] > 0 && (!(Tw[b] > 0.0) || !std::isfinite(Tw[b])))) return SR_EINVAL;
+  double twmax = 0.0;
+  for (int b = 0; b < c->nrep; ++b)
+    if (nwin[b] > 0 && Tw[b] > twmax) twmax = Tw[b];
+  int rc = set_ring(c, ring_length(c, twmax));
+  if (rc != SR_OK) return rc;
+  int* left = (int*)std::malloc((size_t)c->nrep * sizeof(int));
+  if (!left) return SR_ENOMEM;
+  int total_left = 0;
+  for (int b = 0; b < c->nrep; ++b) {
+    left[b] = nwin[b];
+    total_left += nwin[b];
+  }
+  c->last_nwin = 0;
+  rc = SR_OK;
+  while (total_left > 0) {
+    rc = launch_relax(c, Tw, left);
+    if (rc != SR_OK) break;
+    total_left = 0;
+    for (int b = 0; b < c->nrep; ++b) {
+      const int done = (int)c->h_rs[b].windows_done;
+      for (int w = 0; w < done; ++w) c->t_c[b] = c->t_c[b] + Tw[b];
+      left[b] -= done;
+      total_left += left[b];
+      if (b == 0) c->last_nwin += done;
+    }
+    const unsigned status = c->h_st->status;
+    if (status == 0u) {
+      if (total_left != 0) rc = SR_ECUDA;   // the kernel ended early without a reason
+      break;
+    }
+    if (status & ST_TIMEOUT) { rc = SR_TIMEOUT; break; }
+    if (status & ST_NOT_CONVERGED) { rc = SR_NOT_CONVERGED; break; }
+    if (status & ST_CAPACITY) {
+      if (!c->cap_auto || c->cap >= kMaxCap) { rc = SR_CAPACITY; break; }
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) { rc = SR_ECUDA; break; }
+      rc = alloc_history(c, c->cap * 2);
+      if (rc != SR_OK) break;
+      continue;
+    }
+    rc = SR_ECUDA;
+    break;
+  }
+  std::free(left);
+  return rc;
+}
+
+int observables_of(sr_ctx* c, int b, sr_obs* out) {
+  KParams k = make_params(c);
+  if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->h_rs + b, c->rs + b, sizeof(RepStats), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaMemsetAsync(c->obs_i, 0, 2 * sizeof(long long), c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  const RepDesc& d = c->hdesc[b];
+  observe_ints_kernel<<<(d.NR + 255) / 256, 256, 0, c->stream>>>(k, b, c->obs_i);
+  observe_integrals_kernel<<<1, 1024, 0, c->stream>>>(k, b, c->obs_f);
+  if (cudaGetLastError() != cudaSuccess) return SR_ECUDA;
+  c->launches += 2;
+  cudaMemcpyAsync(c->h_obs_i, c->obs_i, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(c->h_obs_f, c->obs_f, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
+  const DevStats& h = *c->h_st;
+  const RepStats& rs = c->h_rs[b];
+  std::memset(out, 0, sizeof *out);
+  out->t_c = c->t_c[b];
+  out->mag = c->h_obs_i[0];
+  out->bonds = c->h_obs_i[1];
+  const double sites = (double)d.L * (double)d.L;
+  out->m = (double)out->mag / sites;
+  out->E = -c->reps[b].J * (double)out->bonds - c->reps[b].h * (double)out->mag;
+  out->int_mag = c->h_obs_f[0];
+  out->int_bonds = c->h_obs_f[1];
+  out->committed = rs.committed;
+  out->generated = rs.generated;
+  out->breaks = rs.breaks;
+  out->windows = rs.windows;
+  out->iterations = rs.iterations;
+  out->last_iters = rs.last_iters;
+  out->max_iters_seen = rs.max_iters_seen;
+  out->max_f = rs.max_f;
+  out->capacity = (uint32_t)c->cap;
+  out->launches = c->launches;
+  out->region_passes = h.region_passes;
+  out->region_skips = h.region_skips;
+  out->run_cycles = h.run_cycles;
+  out->run_cycles_max = h.run_cycles_max;
+  out->slots = h.slots;
+  return SR_OK;
+}
+
+int spins_device_of(sr_ctx* c, int b, int8_t* dev_out, size_t n) {
+  const RepDesc& d = c->hdesc[b];
+  if (!dev_out || n != (size_t)d.L * d.L) return SR_EINVAL;
+  KParams k = make_params(c);
+  unpack_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(k, b, dev_out);
+  c->launches += 1;
+  return cuda_rc(cudaGetLastError());
+}
+
+int spins_host_of(sr_ctx* c, int b, int8_t* host_out, size_t n) {
+  if (!host_out) return SR_EINVAL;
+  int rc = spins_device_of(c, b, c->stage, n);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(host_out, c->stage, n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  return cuda_rc(cudaStreamSynchronize(c->stream));
+}
+
+// Committed clock state of lattice b into caller device buffers (scratch: obs).
+int carry_of(sr_ctx* c, int b, uint64_t* index, double* x, double* bb, double* t_last, size_t n) {
+  const RepDesc& d = c->hdesc[b];
+  if (n != (size_t)d.NR) return SR_EINVAL;
+  unsigned long long* di = nullptr;
+  double *dx = nullptr, *db = nullptr, *dt = nullptr;
+  int rc = SR_OK;
+  if (dalloc(&di, n) || dalloc(&dx, n) || dalloc(&db, n) || dalloc(&dt, n)) rc = SR_ENOMEM;
+  if (rc == SR_OK) {
+    KParams k = make_params(c);
+    gather_carry_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(k, b, di, dx, db, dt);
+    rc = cuda_rc(cudaGetLastError());
+  }
+  if (rc == SR_OK && index) cudaMemcpyAsync(index, di, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (rc == SR_OK && x) cudaMemcpyAsync(x, dx, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (rc == SR_OK && bb) cudaMemcpyAsync(bb, db, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (rc == SR_OK && t_last) cudaMemcpyAsync(t_last, dt, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
+  if (di) cudaFree(di);
+  if (dx) cudaFree(dx);
+  if (db) cudaFree(db);
+  if (dt) cudaFree(dt);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sr_strerror(int code) {
+  switch (code) {
+    case SR_OK: return "ok";
+    case SR_EINVAL: return "invalid argument";
+    case SR_ENOMEM: return "out of memory";
+    case SR_ECUDA: return "CUDA error";
+    case SR_NOT_CONVERGED: return "relaxation did not converge within the iteration cap";
+    case SR_CAPACITY: return "boundary history exceeded the largest capacity";
+    case SR_TIMEOUT: return "grid-wide synchronize timed out";
+    case SR_EUNSUPPORTED: return "unsupported configuration";
+    case SR_ETOOLARGE: return "problem does not fit the fixed no-allocation scratch";
+    default: return "unknown status";
+  }
+}
+
+int sr_create_ex(sr_ctx** out, const sr_params* prm) {
+  if (!out || !prm) return SR_EINVAL;
+  *out = nullptr;
+  sr_replica r;
+  std::memset(&r, 0, sizeof r);
+  r.L = prm->L;
+  r.J = prm->J;
+  r.h = prm->h;
+  r.T = prm->T;
+  r.seed = prm->seed;
+  r.init_mode = prm->init_mode;
+  r.rates = prm->rates;
+  return create_common(out, &r, 1, *prm);
+}
+
+int sr_create_batch(sr_ctx** out, const sr_replica* reps, int n, const sr_params* common) {
+  if (!out || !common) return SR_EINVAL;
+  *out = nullptr;
+  return create_common(out, reps, n, *common);
 }
 
 int sr_create(sr_ctx** out, int L, double J, double h, double T, int region_w, int region_h,
@@ -1993,160 +2367,96 @@ void sr_destroy(sr_ctx* c) {
 
 int sr_run_windows(sr_ctx* c, double t0, double Tw, int n) {
   if (!c || n < 1 || !(Tw > 0.0) || !std::isfinite(Tw)) return SR_EINVAL;
-  if (t0 != c->t_c) return SR_EINVAL;
-  double t = t0;
-  int remaining = n;
-  c->last_nwin = 0;
-  int rc0 = set_ring(c, ring_length(c, Tw));
-  if (rc0 != SR_OK) return rc0;
-  while (remaining > 0) {
-    int rc = launch_relax(c, t, Tw, remaining);
-    if (rc != SR_OK) return rc;
-    const DevStats& h = *c->h_st;
-    const int done = (int)h.windows_done;
-    for (int w = 0; w < done; ++w) t = t + Tw;
-    c->t_c = t;
-    c->last_nwin += done;
-    remaining -= done;
-    if (h.status == 0u) {
-      if (remaining != 0) return SR_ECUDA;   // kernel ended early without a reason
-      break;
+  for (int b = 0; b < c->nrep; ++b)
+    if (t0 != c->t_c[b]) return SR_EINVAL;
+  double* tw = (double*)std::malloc((size_t)c->nrep * sizeof(double));
+  int* nw = (int*)std::malloc((size_t)c->nrep * sizeof(int));
+  int rc = SR_ENOMEM;
+  if (tw && nw) {
+    for (int b = 0; b < c->nrep; ++b) {
+      tw[b] = Tw;
+      nw[b] = n;
     }
-    if (h.status & ST_TIMEOUT) return SR_TIMEOUT;
-    if (h.status & ST_NOT_CONVERGED) return SR_NOT_CONVERGED;
-    if (h.status & ST_CAPACITY) {
-      if (!c->cap_auto || c->cap >= kMaxCap) return SR_CAPACITY;
-      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
-      rc = alloc_history(c, c->cap * 2);
-      if (rc != SR_OK) return rc;
-      continue;
-    }
-    return SR_ECUDA;
+    rc = run_all(c, tw, nw);
   }
-  return SR_OK;
+  std::free(tw);
+  std::free(nw);
+  return rc;
 }
 
 int sr_run_window(sr_ctx* c, double t0, double Tw) { return sr_run_windows(c, t0, Tw, 1); }
 
-int sr_observables(sr_ctx* c, sr_obs* out) {
-  if (!c || !out) return SR_EINVAL;
-  KParams k = make_params(c);
-  if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
-      cudaSuccess)
-    return SR_ECUDA;
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
-  const unsigned cidx = c->h_st->cidx;
-  if (cudaMemsetAsync(c->obs_i, 0, 2 * sizeof(long long), c->stream) != cudaSuccess) return SR_ECUDA;
-  observe_ints_kernel<<<(c->NR + 255) / 256, 256, 0, c->stream>>>(k, cidx, c->obs_i);
-  observe_integrals_kernel<<<1, 1024, 0, c->stream>>>(k, cidx, c->obs_f);
-  if (cudaGetLastError() != cudaSuccess) return SR_ECUDA;
-  c->launches += 2;
-  cudaMemcpyAsync(c->h_obs_i, c->obs_i, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
-  cudaMemcpyAsync(c->h_obs_f, c->obs_f, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
-  const DevStats& h = *c->h_st;
-  std::memset(out, 0, sizeof *out);
-  out->t_c = c->t_c;
-  out->mag = c->h_obs_i[0];
-  out->bonds = c->h_obs_i[1];
-  const double sites = (double)c->prm.L * (double)c->prm.L;
-  out->m = (double)out->mag / sites;
-  out->E = -c->prm.J * (double)out->bonds - c->prm.h * (double)out->mag;
-  out->int_mag = c->h_obs_f[0];
-  out->int_bonds = c->h_obs_f[1];
-  out->committed = h.committed;
-  out->generated = h.generated;
-  out->breaks = h.breaks;
-  out->windows = h.windows;
-  out->iterations = h.iterations;
-  out->last_iters = h.last_iters;
-  out->max_iters_seen = h.max_iters_seen;
-  out->max_f = h.max_f;
-  out->capacity = (uint32_t)c->cap;
-  out->launches = c->launches;
-  out->region_passes = h.region_passes;
-  out->region_skips = h.region_skips;
-  out->run_cycles = h.run_cycles;
-  out->run_cycles_max = h.run_cycles_max;
-  out->slots = h.slots;
-  return SR_OK;
+int sr_run_batch(sr_ctx* c, const double* Tw, const int* n_windows) {
+  if (!c || !Tw || !n_windows) return SR_EINVAL;
+  return run_all(c, Tw, n_windows);
 }
 
-static int committed_index(sr_ctx* c, unsigned* cidx) {
-  if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
-      cudaSuccess)
-    return SR_ECUDA;
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
-  *cidx = c->h_st->cidx;
-  return SR_OK;
+int sr_observables(sr_ctx* c, sr_obs* out) {
+  if (!c || !out) return SR_EINVAL;
+  return observables_of(c, 0, out);
+}
+
+int sr_observables_replica(sr_ctx* c, int replica, sr_obs* out) {
+  if (!c || !out || replica < 0 || replica >= c->nrep) return SR_EINVAL;
+  return observables_of(c, replica, out);
 }
 
 int sr_get_spins_device(sr_ctx* c, int8_t* dev_out, size_t n) {
-  if (!c || !dev_out || n != (size_t)c->prm.L * c->prm.L) return SR_EINVAL;
-  unsigned cidx;
-  int rc = committed_index(c, &cidx);
-  if (rc) return rc;
-  KParams k = make_params(c);
-  unpack_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(k, cidx, dev_out);
-  c->launches += 1;
-  return cuda_rc(cudaGetLastError());
+  if (!c) return SR_EINVAL;
+  return spins_device_of(c, 0, dev_out, n);
 }
 
 int sr_get_spins(sr_ctx* c, int8_t* host_out, size_t n) {
-  if (!c || !host_out) return SR_EINVAL;
-  int rc = sr_get_spins_device(c, c->stage, n);
-  if (rc) return rc;
-  if (cudaMemcpyAsync(host_out, c->stage, n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-    return SR_ECUDA;
-  return cuda_rc(cudaStreamSynchronize(c->stream));
+  if (!c) return SR_EINVAL;
+  return spins_host_of(c, 0, host_out, n);
+}
+
+int sr_get_spins_replica(sr_ctx* c, int replica, int8_t* host_out, size_t n) {
+  if (!c || replica < 0 || replica >= c->nrep) return SR_EINVAL;
+  return spins_host_of(c, replica, host_out, n);
 }
 
 int sr_set_spins_device(sr_ctx* c, const int8_t* dev_in, size_t n) {
-  if (!c || !dev_in || n != (size_t)c->prm.L * c->prm.L) return SR_EINVAL;
-  return init_state(c, dev_in);
+  if (!c || !dev_in || n != (size_t)c->hdesc[0].L * c->hdesc[0].L) return SR_EINVAL;
+  return init_state(c, 0, dev_in);
 }
 
 int sr_set_spins(sr_ctx* c, const int8_t* host_in, size_t n) {
-  if (!c || !host_in || n != (size_t)c->prm.L * c->prm.L) return SR_EINVAL;
+  if (!c || !host_in || n != (size_t)c->hdesc[0].L * c->hdesc[0].L) return SR_EINVAL;
   if (cudaMemcpyAsync(c->stage, host_in, n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     return SR_ECUDA;
-  int rc = init_state(c, c->stage);
+  int rc = init_state(c, 0, c->stage);
   if (rc) return rc;
   return cuda_rc(cudaStreamSynchronize(c->stream));
 }
 
 int sr_reset(sr_ctx* c) {
   if (!c) return SR_EINVAL;
-  int rc = init_state(c, nullptr);
+  int rc = init_state(c, -1, nullptr);
   if (rc) return rc;
   return cuda_rc(cudaStreamSynchronize(c->stream));
 }
 
 int sr_get_carry(sr_ctx* c, uint64_t* index, double* x, double* b, double* t_last, size_t n) {
-  if (!c || n != (size_t)c->NR) return SR_EINVAL;
-  unsigned cidx;
-  int rc = committed_index(c, &cidx);
-  if (rc) return rc;
-  const size_t off = (size_t)cidx * c->NR;
-  if (index) cudaMemcpyAsync(index, c->ci + off, n * 8, cudaMemcpyDeviceToHost, c->stream);
-  if (x) cudaMemcpyAsync(x, c->cx + off, n * 8, cudaMemcpyDeviceToHost, c->stream);
-  if (b) cudaMemcpyAsync(b, c->cb + off, n * 8, cudaMemcpyDeviceToHost, c->stream);
-  if (t_last) cudaMemcpyAsync(t_last, c->ct + off, n * 8, cudaMemcpyDeviceToHost, c->stream);
-  return cuda_rc(cudaStreamSynchronize(c->stream));
+  if (!c) return SR_EINVAL;
+  return carry_of(c, 0, index, x, b, t_last, n);
+}
+
+int sr_get_carry_replica(sr_ctx* c, int replica, uint64_t* index, double* x, double* b,
+                         double* t_last, size_t n) {
+  if (!c || replica < 0 || replica >= c->nrep) return SR_EINVAL;
+  return carry_of(c, replica, index, x, b, t_last, n);
 }
 
 int sr_get_trace(sr_ctx* c, uint64_t* lens, double* times, uint32_t* sites, size_t n_regions,
                  size_t cap) {
-  if (!c || n_regions != (size_t)c->NR) return SR_EINVAL;
+  if (!c || n_regions != (size_t)c->hdesc[0].NR) return SR_EINVAL;
   if ((times || sites) && (c->prm.trace_capacity == 0 || cap != (size_t)c->prm.trace_capacity))
     return SR_EINVAL;
-  unsigned cidx;
-  int rc = committed_index(c, &cidx);
+  int rc = SR_OK;
+  if (lens) rc = carry_of(c, 0, lens, nullptr, nullptr, nullptr, n_regions);
   if (rc) return rc;
-  const size_t total = n_regions * cap;
-  if (lens)
-    cudaMemcpyAsync(lens, c->ci + (size_t)cidx * c->NR, n_regions * 8, cudaMemcpyDeviceToHost,
-                    c->stream);
+  const size_t total = n_regions * cap;     // lattice 0 holds regions 0 .. NR0 - 1
   if (times) cudaMemcpyAsync(times, c->trt, total * 8, cudaMemcpyDeviceToHost, c->stream);
   if (sites) cudaMemcpyAsync(sites, c->trs, total * 4, cudaMemcpyDeviceToHost, c->stream);
   return cuda_rc(cudaStreamSynchronize(c->stream));
@@ -2165,10 +2475,9 @@ int sr_get_window_iters(sr_ctx* c, uint32_t* out, size_t n) {
     std::free(tmp);
     return SR_ECUDA;
   }
-  // the last launch wrote windows 0.. of its own count; a retried call
-  // (capacity growth) restarts the ring at 0, so the last m entries written
-  // are the last windows of the final launch
-  const int last_launch = (int)c->h_st->windows_done;
+  // window w of the last launch is at w; a retried call (capacity growth)
+  // restarts at 0, so the last m entries of the final launch are the last windows
+  const int last_launch = (int)c->h_rs[0].windows_done;
   for (int i = 0; i < m; ++i) {
     const int w = last_launch - m + i;
     out[i] = tmp[((w % kWinRing) + kWinRing) % kWinRing];
@@ -2218,10 +2527,10 @@ int sr_eval_softfloat(int op, const double* a, const double* b, double* out, siz
 int sr_get_info(sr_ctx* c, int* n_regions, int* frac_bits, uint64_t* P, int* threads_per_block,
                 int* blocks) {
   if (!c) return SR_EINVAL;
-  if (n_regions) *n_regions = c->NR;
+  if (n_regions) *n_regions = c->hdesc[0].NR;
   if (frac_bits) *frac_bits = c->F;
   if (P)
-    for (int k = 0; k < 10; ++k) P[k] = c->P[k];
+    for (int k = 0; k < 10; ++k) P[k] = c->hdesc[0].P[k];
   if (threads_per_block) *threads_per_block = c->rl;
   if (blocks) *blocks = c->blocks;
   return SR_OK;
@@ -2281,26 +2590,46 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   if (region_w > 32 || region_h > 32) return SR_EUNSUPPORTED;
 
   // the same context a sr_create_ex would build, without any allocation
+  sr_replica rp;
+  std::memset(&rp, 0, sizeof rp);
+  rp.L = L;
+  rp.J = J;
+  rp.h = h;
+  rp.T = T;
+  rp.seed = seed;
+  rp.init_mode = SR_INIT_FAIR_COIN;
+  rp.rates = SR_RATES_METROPOLIS;
+  RepDesc hd;
+  std::memset(&hd, 0, sizeof hd);
+  double t_c = 0.0;
   sr_ctx c;
   std::memset(&c, 0, sizeof c);
   c.prm.L = L;
-  c.prm.J = J;
-  c.prm.h = h;
-  c.prm.T = T;
   c.prm.region_w = region_w;
   c.prm.region_h = region_h;
-  c.prm.seed = seed;
-  c.prm.init_mode = SR_INIT_FAIR_COIN;
-  c.prm.rates = SR_RATES_METROPOLIS;
   c.prm.max_iters = 1 << 16;
   c.prm.barrier_timeout_ms = 2000;
   c.prm.test_barrier_skip_block = -1;
-  c.NX = L / region_w;
-  c.NY = L / region_h;
-  c.NR = c.NX * c.NY;
+  c.nrep = 1;
+  c.reps = &rp;
+  c.hdesc = &hd;
+  c.t_c = &t_c;
   c.F = 63 - bitlen((long long)region_w * region_h);
   c.scale = std::ldexp(1.0, -c.F);
-  rate_table(c.prm, c.F, c.P);
+  hd.L = L;
+  hd.NX = L / region_w;
+  hd.NY = L / region_h;
+  hd.NR = hd.NX * hd.NY;
+  hd.off = 0;
+  hd.spans_x = hd.NX == 1;
+  hd.spans_y = hd.NY == 1;
+  hd.key0 = (uint32_t)seed;
+  hd.key1 = (uint32_t)(seed >> 32);
+  hd.init_mode = SR_INIT_FAIR_COIN;
+  rate_table(rp, c.F, hd.P);
+  for (int k = 0; k < 10; ++k) hd.Rp[k] = hd.P[k] ? ~0ull / hd.P[k] : 0ull;
+  c.NR = hd.NR;
+  c.Lmax = L;
   c.stream = (cudaStream_t)stream;
 
   // size check before touching the GPU
@@ -2318,6 +2647,12 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   probe.take<unsigned long long>(nr);             // ring ends
   probe.take<DevStats>(1);
   probe.take<uint32_t>(kWinRing);
+  probe.take<RepDesc>(1);                         // lattice descriptor and counters
+  probe.take<RepStats>(1);
+  probe.take<uint32_t>(3);                        // convergence flags
+  probe.take<uint32_t>(3 * nr);                   // lattice, iteration, window of each region
+  probe.take<double>(nr);                         // window start of each region
+  probe.take<uint8_t>(2 * nr);                    // committed copy, ring top-up pending
   if (probe.used > (size_t)SR_NOALLOC_SCRATCH_BYTES) return SR_ETOOLARGE;
 
   int dev = 0;
@@ -2347,6 +2682,15 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.rhi = cv.take<unsigned long long>(nr);
   c.st = cv.take<DevStats>(1);
   c.win_iters = cv.take<uint32_t>(kWinRing);
+  c.desc = cv.take<RepDesc>(1);
+  c.rs = cv.take<RepStats>(1);
+  c.rflags = cv.take<uint32_t>(3);
+  c.rrep = cv.take<uint32_t>(nr);
+  c.rn = cv.take<uint32_t>(nr);
+  c.rwin = cv.take<uint32_t>(nr);
+  c.rts = cv.take<double>(nr);
+  c.rcidx = cv.take<uint8_t>(nr);
+  c.rfill = cv.take<uint8_t>(nr);
   c.cap = kNoallocCap;
   c.K = kNoallocRing;
   c.Kcap = kNoallocRing;
@@ -2377,38 +2721,47 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.blocks = blocks;
 
   // the shared scratch keeps the previous call's contents: start from zero
-  // where the kernels expect it (counters, barrier, flags, list lengths, rings)
-  if (cudaMemsetAsync(c.hl, 0, 2 * 4 * nr * sizeof(uint32_t), c.stream) != cudaSuccess)
+  // where the kernels expect it (list lengths; every region is lattice 0)
+  if (cudaMemsetAsync(c.hl, 0, 2 * 4 * nr * sizeof(uint32_t), c.stream) != cudaSuccess ||
+      cudaMemsetAsync(c.rrep, 0, nr * sizeof(uint32_t), c.stream) != cudaSuccess)
     return SR_ECUDA;
-  rc = init_state(&c, spins_in);            // spins, halos, clocks, counters, rings
+  rc = init_state(&c, 0, spins_in);         // spins, halos, clocks, counters, rings
   if (rc != SR_OK) return rc;
 
-  // one persistent launch for all windows, then read the status word
+  // one persistent launch for all windows, then read the status words
+  hd.t0 = 0.0;
+  hd.Tw = Tw;
+  hd.nwin = n_windows;
+  if (cudaMemcpyAsync(c.desc, &hd, sizeof hd, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
+      cudaMemsetAsync(c.st, 0, offsetof(DevStats, region_passes), c.stream) != cudaSuccess ||
+      cudaMemsetAsync(c.rflags, 0, 3 * sizeof(uint32_t), c.stream) != cudaSuccess)
+    return SR_ECUDA;
   KParams k = make_params(&c);
-  k.t0 = 0.0;
-  k.Tw = Tw;
-  k.nwin = n_windows;
-  if (cudaMemsetAsync(c.st, 0, offsetof(DevStats, cidx), c.stream) != cudaSuccess) return SR_ECUDA;
   void* args[] = {&k};
   if (cudaLaunchCooperativeKernel((const void*)relax_kernel<0>, dim3(c.blocks), dim3(c.tpb), args,
-                                  c.smem, c.stream) != cudaSuccess)
+                                  c.smem, c.stream) != cudaSuccess) {
+    cudaGetLastError();
     return SR_ECUDA;
+  }
   DevStats hs;
+  RepStats hr;
   if (cudaMemcpyAsync(&hs, c.st, sizeof hs, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+      cudaMemcpyAsync(&hr, c.rs, sizeof hr, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
       cudaStreamSynchronize(c.stream) != cudaSuccess)
     return SR_ECUDA;
   if (hs.status & ST_TIMEOUT) return SR_TIMEOUT;
   if (hs.status & ST_NOT_CONVERGED) return SR_NOT_CONVERGED;
   if (hs.status & ST_CAPACITY) return SR_CAPACITY;
-  if (hs.status != 0u || (int)hs.windows_done != n_windows) return SR_ECUDA;
+  if (hs.status != 0u || (int)hr.windows_done != n_windows) return SR_ECUDA;
 
   // outputs
-  unpack_rows_kernel<<<(unsigned)(((size_t)L * L + 255) / 256), 256, 0, c.stream>>>(k, hs.cidx,
-                                                                                    spins_out);
+  unpack_rows_kernel<<<(unsigned)(((size_t)L * L + 255) / 256), 256, 0, c.stream>>>(k, 0, spins_out);
   if (cudaGetLastError() != cudaSuccess) return SR_ECUDA;
-  if (counts_out &&
-      cudaMemcpyAsync(counts_out, c.ci + (size_t)hs.cidx * nr, nr * sizeof(unsigned long long),
-                      cudaMemcpyDeviceToDevice, c.stream) != cudaSuccess)
-    return SR_ECUDA;
+  if (counts_out) {
+    // committed event index of each region = its committed events
+    gather_carry_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, c.stream>>>(
+        k, 0, (unsigned long long*)counts_out, nullptr, nullptr, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return SR_ECUDA;
+  }
   return cuda_rc(cudaStreamSynchronize(c.stream));
 }

@@ -1,0 +1,139 @@
+"""Batches of independent lattices in one persistent launch, each lattice
+against the oracle's run of that lattice alone.
+
+Each lattice of a batch follows the synchronous-relaxation procedure of §4 on
+its own (its own windows, iterations and fixed point), so its trajectory must
+be bit-identical to the single-lattice run: spins, per-region event counts,
+the clock carry and the exact integer observables."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+sr = pytest.importorskip("paper_cs_0405053_gb300")
+
+INIT = {"fair": oracle.INIT_FAIR_COIN, "up": oracle.INIT_ALL_UP, "down": oracle.INIT_ALL_DOWN}
+
+
+def _ends(Tw, n):
+    out, t = [], 0.0
+    for _ in range(n):
+        t = t + Tw
+        out.append(t)
+    return out
+
+
+def _check_lattice(batch, b, W, H, Tw, nwin_total):
+    r = batch.replicas[b]
+    ends = _ends(Tw, nwin_total) if nwin_total else [0.0]
+    ref = oracle.run(r.L, r.J, r.h, r.T, W, H, r.seed, ends, init_mode=INIT[r.init],
+                     glauber=(r.rates == "glauber"))
+    assert np.array_equal(batch.spins(b), ref.spins[-1]), f"spins of lattice {b}"
+    i, x, bb, t = batch.carry(b)
+    if nwin_total:
+        assert np.array_equal(i, ref.carry_i), f"event index of lattice {b}"
+        assert np.array_equal(x, ref.carry_x)
+        assert np.array_equal(bb, ref.carry_b)
+        assert np.array_equal(t, ref.carry_t)
+    else:
+        assert not i.any() and not bb.any() and not t.any()
+    o = batch.observables(b)
+    assert o.mag == ref.mag[-1] and o.bonds == ref.bonds[-1]
+    assert o.committed == int(ref.counts[-1].sum())
+    assert o.windows == nwin_total
+    assert o.t_c == (ends[-1] if nwin_total else 0.0)
+
+
+REPS = [dict(L=32, J=1.0, h=0.05, T=1.5, seed=11),
+        dict(L=16, J=0.8, h=-0.2, T=1.2, seed=12, rates="glauber", init="down"),
+        dict(L=48, J=1.0, h=0.0, T=2.269, seed=13, init="up"),
+        dict(L=24, J=1.0, h=0.2, T=3.5, seed=14),
+        dict(L=8, J=1.0, h=0.0, T=1.0, seed=15),
+        dict(L=40, J=0.0, h=0.3, T=2.0, seed=16)]
+TW = [1.0, 0.5, 0.25, 2.0, 0.7, 1.0]
+NW = [3, 5, 2, 1, 4, 0]
+
+MAPS = [dict(),
+        dict(lanes_per_region=1, lanes_per_warp=3, time_arith=2),
+        dict(lanes_per_region=1, lanes_per_warp=32, time_arith=1, replay_records=2),
+        dict(lanes_per_region=32)]
+
+
+@pytest.mark.parametrize("m", range(len(MAPS)))
+def test_mixed_batch_bit_exact(m):
+    with sr.Batch(REPS, region=(8, 8), **MAPS[m]) as batch:
+        batch.run(TW, NW)
+        for b in range(len(REPS)):
+            _check_lattice(batch, b, 8, 8, TW[b], NW[b])
+
+
+@pytest.mark.parametrize("m", range(len(MAPS)))
+def test_batch_runs_continue(m):
+    """Two run calls with different window counts: each lattice continues
+    from its own committed time."""
+    with sr.Batch(REPS, region=(8, 8), **MAPS[m]) as batch:
+        batch.run(TW, NW)
+        more = [1, 0, 3, 2, 1, 2]
+        batch.run(TW, more)
+        for b in range(len(REPS)):
+            _check_lattice(batch, b, 8, 8, TW[b], NW[b] + more[b])
+        assert batch.t_c[5] == _ends(TW[5], 2)[-1]
+
+
+def test_many_small_lattices():
+    """Sixty lattices of 4 regions each, spread over blocks and lanes."""
+    reps = [dict(L=16, J=1.0, h=0.05 * ((b % 5) - 2), T=1.0 + 0.05 * b, seed=100 + b)
+            for b in range(60)]
+    nw = [1 + (b % 4) for b in range(60)]
+    with sr.Batch(reps, region=(8, 8)) as batch:
+        batch.run(0.5, nw)
+        for b in range(60):
+            _check_lattice(batch, b, 8, 8, 0.5, nw[b])
+
+
+def test_batch_equals_separate_lattices():
+    """Observables and counters of a lattice in a batch equal those of the
+    same lattice simulated alone."""
+    reps = REPS[:4]
+    with sr.Batch(reps, region=(8, 8)) as batch:
+        batch.run(TW[:4], NW[:4])
+        for b, r in enumerate(reps):
+            lat = sr.Lattice(r["L"], r["J"], r["h"], r["T"], (8, 8), seed=r["seed"],
+                             init=r.get("init", "fair"), rates=r.get("rates", "metropolis"))
+            lat.run_windows(TW[b], NW[b])
+            o1, o2 = batch.observables(b), lat.observables()
+            assert np.array_equal(batch.spins(b), lat.spins())
+            for f in ("t_c", "mag", "bonds", "committed", "generated", "breaks", "windows",
+                      "iterations", "max_iters_seen", "max_f", "int_mag", "int_bonds"):
+                assert getattr(o1, f) == getattr(o2, f), f
+            lat.close()
+
+
+def test_batch_capacity_growth():
+    """Long windows at high temperature overflow the initial history capacity
+    of one lattice; the retry re-runs only what did not commit."""
+    reps = [dict(L=32, T=3.5, h=0.0, seed=21), dict(L=16, T=1.0, h=0.1, seed=22)]
+    with sr.Batch(reps, region=(16, 16)) as batch:
+        batch.run([8.0, 1.0], [2, 3])
+        assert batch.observables(0).capacity > 64
+        _check_lattice(batch, 0, 16, 16, 8.0, 2)
+        _check_lattice(batch, 1, 16, 16, 1.0, 3)
+
+
+def test_batch_reset_and_bad_arguments():
+    with sr.Batch(REPS[:2], region=(8, 8)) as batch:
+        batch.run(1.0, 2)
+        s0 = batch.spins(0)
+        batch.reset()
+        batch.run(1.0, 2)
+        assert np.array_equal(batch.spins(0), s0)
+        with pytest.raises(sr.SRError):
+            batch.run([1.0, -1.0], [1, 1])
+        with pytest.raises(sr.SRError):
+            batch.observables(2)
+    with pytest.raises(sr.SRError):
+        sr.Batch([dict(L=20)], region=(8, 8))      # 20 is not a multiple of 8
+    with pytest.raises(sr.SRError):
+        sr.Batch([], region=(8, 8))
