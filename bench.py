@@ -138,6 +138,79 @@ def run_reference(args):
     return 0
 
 
+def _batched_vs_plain(args, sr, torch, stream):
+    """The batched workload: 256 independent lattices (L uniform over
+    {64 .. 1024}, T uniform in [1, 3.5], h uniform in [-0.2, 0.2], J = 1,
+    fair-coin spins) run to t = args.batch_t in one context, with the region
+    shape, lanes per warp and events per window chosen by the autotuner and
+    window lengths matched to each lattice's event rate; against the same
+    lattices run one per context (a stratified sample of every 8th lattice)."""
+    from paper_cs_0405053_gb300 import workloads
+    reps = workloads.batch_replicas()
+    t0 = time.perf_counter()
+    tune = sr.autotune(reps, t_trial=1.0)
+    tune_s = time.perf_counter() - t0
+    t_end = float(args.batch_t)
+
+    def timed(b, lpw):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        ev0.record(stream)
+        b.run_adaptive(t_end, kappa=tune.kappa)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        obs = [b.observables(k) for k in range(len(b))]
+        return ev0.elapsed_time(ev1) * 1e-3, wall, obs
+
+    bt = sr.Batch(reps, region=tune.region, lanes_per_warp=tune.lanes_per_warp)
+    bt.run_adaptive(min(1.0, t_end), kappa=tune.kappa)      # warm-up
+    bt.reset()
+    clock_path = os.path.join(tempfile.gettempdir(), f"sr_clocks_batch_{os.getpid()}.csv")
+    sampler = _clock_sampler(clock_path)
+    time.sleep(0.3 if sampler else 0)
+    dev_s, wall_s, obs = timed(bt, tune.lanes_per_warp)
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    committed = sum(o.committed for o in obs)
+    generated = sum(o.generated for o in obs)
+    iters = sum(o.iterations for o in obs) / max(1, sum(o.windows for o in obs))
+    launches = obs[0].launches
+    bt.close()
+    batched = committed / dev_s
+
+    sample = list(range(0, len(reps), 8))
+    p_com, p_s = 0, 0.0
+    for k in sample:
+        one = sr.Batch([reps[k]], region=tune.region)
+        d, _, o = timed(one, 0)
+        p_com += o[0].committed
+        p_s += d
+        one.close()
+    plain = p_com / p_s
+    ops = committed * OPS_PER_EVENT / dev_s
+    return {
+        "workload": "256 lattices: L uniform over {64,128,256,512,1024}, T uniform in [1,3.5], "
+                    "h uniform in [-0.2,0.2], J=1, fair-coin spins, Metropolis, run to "
+                    f"t={t_end:g} each (numpy Philox key 4, seeds 1000+b)",
+        "sites": int(sum(r["L"] ** 2 for r in reps)),
+        "tuning": {"region": list(tune.region), "lanes_per_warp": tune.lanes_per_warp or "auto",
+                   "kappa": tune.kappa, "trials": tune.trials, "seconds": round(tune_s, 2)},
+        "batched": {"flips_per_s": batched, "s": dev_s, "wall_s": wall_s, "committed": committed,
+                    "generated": generated, "wasted_ratio": (generated - committed) / committed,
+                    "iters_mean": iters, "launches": launches},
+        "one_by_one": {"flips_per_s": plain, "s": p_s, "committed": p_com,
+                       "sample": f"every 8th lattice ({len(sample)} of {len(reps)}), each in its "
+                                 "own context with the same shape and window rule"},
+        "batched_over_one_by_one": batched / plain,
+        "clocks": _clock_summary(clock_path, torch.cuda.current_device()),
+        "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": INT_PEAK_OPS / 1e12,
+                     "unit": "Tops/s", "frac": ops / INT_PEAK_OPS},
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -258,6 +331,7 @@ def run_ours(args):
     # (boundary fraction of 16x16 regions at uniform rates, 60/256)
     hbm_bound_events = HBM_GBS * 1e9 / (HIST_BYTES_PER_BOUNDARY_EVENT * 60 / 256)
     cpu_committed, cpu_dt = _oracle_baseline()
+    batch_info = None if args.no_batch else _batched_vs_plain(args, sr, torch, stream)
     tw_detail = {}
     for Tw in WINDOWS:
         ms, kms_tw, o, iters = per_tw[Tw][-1]
@@ -293,6 +367,7 @@ def run_ours(args):
                          "sample": "full workload trajectory to t=100 (one run; the oracle's "
                                    "trajectory does not depend on window ends)"},
         "clocks": _clock_summary(clock_path, local),
+        "batched": batch_info,
         "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)
@@ -348,6 +423,9 @@ def main():
                     help="lanes per region: 1, 32 or 0 (automatic)")
     ap.add_argument("--lpw", type=int, default=0, help="region lanes per warp (lane mapping)")
     ap.add_argument("--arith", type=int, default=0, help="time arithmetic: 1 FP64, 2 integer")
+    ap.add_argument("--batch-t", type=float, default=100.0,
+                    help="simulated time of the batched section")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
     ap.add_argument("--replay", type=int, default=0,
                     help="checkpoint records per region for incremental replay (0 auto, -1 off)")
     args = ap.parse_args()

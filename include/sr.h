@@ -76,8 +76,6 @@ typedef struct sr_params {
                                    0 = automatic */
   int threads_per_block;        /* region slots per block (lanes, or warps with a warp per
                                    region); 0 = automatic */
-  int block_threads;            /* threads per block, >= region lanes; the extra threads help
-                                   draw the presimulated random pairs; 0 = automatic */
   int blocks;                   /* 0 = automatic (all regions resident if they fit) */
   int barrier_timeout_ms;       /* bound on each grid-wide wait; 0 = 2000 */
   int replay_records;           /* incremental replay (one lane per region): checkpoints kept per
@@ -186,6 +184,55 @@ int sr_create_batch(sr_ctx** out, const sr_replica* reps, int n, const sr_params
  * entries.  Errors as sr_run_windows; on error every lattice keeps the state of
  * its last converged window. */
 int sr_run_batch(sr_ctx* ctx, const double* Tw, const int* n_windows);
+
+/* ---- window lengths matched to event rates ----
+ * The paper leaves T_max free (§4, §6: the cost per step grows with the
+ * boundary events f per region and the iterations g).  Window ends are not
+ * break points, so the trajectory does not depend on the window lengths; only
+ * the cost does.  The adaptive runner sizes each lattice's windows so that a
+ * region sees about `kappa` committed events per window. */
+typedef struct sr_adapt {
+  double kappa;                 /* target committed events per region per window; 0 = 8 */
+  double chunk;                 /* simulated time between window-length updates; 0 = 1 */
+  double tw_first;              /* window length of a lattice's first chunk; 0 = 1/16 */
+  double tw_min;                /* smallest window length; 0 = 2^-10 */
+  double tw_max;                /* largest window length; 0 = chunk */
+} sr_adapt;
+
+/* Advance every lattice b from its committed time to t_end[b] (>= t_c; equal
+ * means nothing to do) in chunks of `chunk` time units, all lattices of a
+ * chunk in one persistent launch.  In each chunk lattice b runs windows of
+ * length Tw_b = 2^round(log2(kappa / rho_b)) clamped to [tw_min, tw_max], with
+ * rho_b its committed events per region per unit time in its previous chunk
+ * (tw_first before it has one); a chunk ends early at t_end[b].  Window ends
+ * are then sums of powers of two, exact in double for dyadic t_c and t_end.
+ * opts may be NULL (all defaults).  last_tw (host, n entries, may be NULL)
+ * receives each lattice's last window length.  Errors as sr_run_batch, plus
+ * SR_EINVAL for t_end[b] < t_c or non-positive / non-finite options. */
+int sr_run_batch_adaptive(sr_ctx* ctx, const double* t_end, const sr_adapt* opts, double* last_tw);
+
+/* ---- autotuner ----
+ * Chooses, for a batch of lattices, the region shape (among 8x8, 16x16,
+ * 32x32, 16x8 and 32x16 that divide every L), the region lanes per warp
+ * (automatic, 8, 16, 32) and kappa (4, 8, 16) by timing trial runs of the real
+ * lattices: each trial creates a context, runs the adaptive runner untimed to
+ * t_trial / 2, then timed to t_trial, and scores committed flips per second.
+ * One coordinate at a time (shape, then kappa, then lanes per warp).  The
+ * trajectory of a lattice depends on its region shape (its random streams
+ * are per region) but not on the other two choices.  common supplies every
+ * other setting (as in sr_create_batch; region_w / region_h ignored).
+ * t_trial > 0; 0 = 1.0.  Blocks until done; allocates and frees contexts.
+ * Errors: those of sr_create_batch and sr_run_batch_adaptive; SR_EUNSUPPORTED
+ * when no candidate shape divides every L. */
+typedef struct sr_tune {
+  int region_w, region_h;       /* chosen region shape */
+  int lanes_per_warp;           /* chosen region lanes per warp (0 = automatic) */
+  double kappa;                 /* chosen target events per region per window */
+  double flips_per_s;           /* trial throughput of the choice */
+  int trials;                   /* configurations timed */
+} sr_tune;
+int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t_trial,
+                sr_tune* out);
 
 /* Observables of lattice `replica` (0 <= replica < n).  Errors: SR_EINVAL,
  * SR_ECUDA. */

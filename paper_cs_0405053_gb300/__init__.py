@@ -18,8 +18,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["SRError", "Lattice", "Batch", "Replica", "Observables", "library", "eval_draws",
-           "SR_OK"]
+__all__ = ["SRError", "Lattice", "Batch", "Replica", "Observables", "Tuning", "autotune",
+           "library", "eval_draws", "SR_OK"]
 
 SR_OK, SR_EINVAL, SR_ENOMEM, SR_ECUDA = 0, -1, -2, -3
 SR_NOT_CONVERGED, SR_CAPACITY, SR_TIMEOUT, SR_EUNSUPPORTED = -4, -5, -6, -7
@@ -39,7 +39,7 @@ class _Params(C.Structure):
                 ("init_mode", C.c_int), ("rates", C.c_int), ("capacity", C.c_int),
                 ("max_iters", C.c_int), ("trace_capacity", C.c_int),
                 ("lanes_per_region", C.c_int), ("lanes_per_warp", C.c_int), ("time_arith", C.c_int),
-                ("threads_per_block", C.c_int), ("block_threads", C.c_int), ("blocks", C.c_int),
+                ("threads_per_block", C.c_int), ("blocks", C.c_int),
                 ("barrier_timeout_ms", C.c_int), ("replay_records", C.c_int),
                 ("test_barrier_skip_block", C.c_int),
                 ("stream", C.c_void_p)]
@@ -60,6 +60,16 @@ class Replica:
     seed: int = 1
     init: str = "fair"
     rates: str = "metropolis"
+
+
+class _Adapt(C.Structure):
+    _fields_ = [("kappa", C.c_double), ("chunk", C.c_double), ("tw_first", C.c_double),
+                ("tw_min", C.c_double), ("tw_max", C.c_double)]
+
+
+class _Tune(C.Structure):
+    _fields_ = [("region_w", C.c_int), ("region_h", C.c_int), ("lanes_per_warp", C.c_int),
+                ("kappa", C.c_double), ("flips_per_s", C.c_double), ("trials", C.c_int)]
 
 
 class _Obs(C.Structure):
@@ -138,6 +148,9 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_observables_replica": (C.c_int, [_P, C.c_int, C.POINTER(_Obs)]),
             "sr_get_spins_replica": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
             "sr_get_carry_replica": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_size_t]),
+            "sr_run_batch_adaptive": (C.c_int, [_P, _P, C.POINTER(_Adapt), _P]),
+            "sr_autotune": (C.c_int, [_P, C.c_int, C.POINTER(_Params), C.c_double,
+                                      C.POINTER(_Tune)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -191,7 +204,6 @@ class Lattice:
                  rates: str = "metropolis", capacity: int = 0, max_iters: int = 0,
                  trace_capacity: int = 0, lanes_per_region: int = 0, lanes_per_warp: int = 0,
                  time_arith: int = 0, threads_per_block: int = 0,
-                 block_threads: int = 0,
                  blocks: int = 0,
                  barrier_timeout_ms: int = 0, replay_records: int = 0,
                  test_barrier_skip_block: int = -1,
@@ -205,8 +217,7 @@ class Lattice:
         self.trace_capacity = trace_capacity
         prm = _Params(L, J, h, T, region[0], region[1], seed, INIT_MODES[init], RATES[rates],
                       capacity, max_iters, trace_capacity, lanes_per_region, lanes_per_warp,
-                      time_arith, threads_per_block,
-                      block_threads, blocks,
+                      time_arith, threads_per_block, blocks,
                       barrier_timeout_ms, replay_records, test_barrier_skip_block, stream)
         self._ctx = _P()
         _check(lib.sr_create_ex(C.byref(self._ctx), C.byref(prm)), "sr_create_ex")
@@ -315,6 +326,46 @@ class Lattice:
         return out[:m]
 
 
+def _common_params(region, capacity=0, max_iters=0, lanes_per_region=0, lanes_per_warp=0,
+                   time_arith=0, threads_per_block=0, blocks=0, barrier_timeout_ms=0,
+                   replay_records=0, stream=None) -> _Params:
+    return _Params(0, 0.0, 0.0, 0.0, region[0], region[1], 0, 0, 0, capacity, max_iters, 0,
+                   lanes_per_region, lanes_per_warp, time_arith, threads_per_block, blocks,
+                   barrier_timeout_ms, replay_records, -1, stream)
+
+
+def _replica_array(replicas):
+    reps = [r if isinstance(r, Replica) else Replica(**r) for r in replicas]
+    arr = (_Replica * len(reps))(*[
+        _Replica(r.L, r.J, r.h, r.T, r.seed, INIT_MODES[r.init], RATES[r.rates]) for r in reps])
+    return reps, arr
+
+
+@dataclass
+class Tuning:
+    """Choice of the autotuner (sr_autotune)."""
+    region: Tuple[int, int]
+    lanes_per_warp: int
+    kappa: float
+    flips_per_s: float
+    trials: int
+
+
+def autotune(replicas, t_trial: float = 1.0, **settings) -> Tuning:
+    """Region shape, region lanes per warp and events per window for a batch,
+    chosen by timing short trial runs of these lattices on the GPU."""
+    lib = library()
+    _, arr = _replica_array(replicas)
+    stream = settings.pop("stream", None)
+    if stream is None:
+        stream = _torch_stream()
+    prm = _common_params((16, 16), stream=stream, **settings)
+    t = _Tune()
+    _check(lib.sr_autotune(C.cast(arr, C.c_void_p), len(arr), C.byref(prm), t_trial, C.byref(t)),
+           "sr_autotune")
+    return Tuning((t.region_w, t.region_h), t.lanes_per_warp, t.kappa, t.flips_per_s, t.trials)
+
+
 class Batch:
     """Independent lattices simulated together: every lattice follows the
     synchronous-relaxation procedure on its own (own windows, iterations and
@@ -329,14 +380,11 @@ class Batch:
         lib = library()
         if stream is None and use_torch_stream:
             stream = _torch_stream()
-        self.replicas = [r if isinstance(r, Replica) else Replica(**r) for r in replicas]
+        self.replicas, arr = _replica_array(replicas)
         self.region = region
-        arr = (_Replica * len(self.replicas))(*[
-            _Replica(r.L, r.J, r.h, r.T, r.seed, INIT_MODES[r.init], RATES[r.rates])
-            for r in self.replicas])
-        prm = _Params(0, 0.0, 0.0, 0.0, region[0], region[1], 0, 0, 0, capacity, max_iters, 0,
-                      lanes_per_region, lanes_per_warp, time_arith, threads_per_block, 0, blocks,
-                      barrier_timeout_ms, replay_records, -1, stream)
+        prm = _common_params(region, capacity, max_iters, lanes_per_region, lanes_per_warp,
+                             time_arith, threads_per_block, blocks, barrier_timeout_ms,
+                             replay_records, stream)
         self._arr = arr
         self._ctx = _P()
         _check(lib.sr_create_batch(C.byref(self._ctx), C.cast(arr, C.c_void_p), len(arr),
@@ -379,6 +427,20 @@ class Batch:
         for b in range(n):
             self.t_c[b] = self.observables(b).t_c
         _check(code, "sr_run_batch")
+
+    def run_adaptive(self, t_end, kappa: float = 0.0, chunk: float = 0.0, tw_first: float = 0.0,
+                     tw_min: float = 0.0, tw_max: float = 0.0) -> np.ndarray:
+        """Advance every lattice to t_end[b] with window lengths matched to its
+        event rate; returns each lattice's last window length."""
+        n = len(self.replicas)
+        te = np.ascontiguousarray(np.broadcast_to(np.asarray(t_end, dtype=np.float64), (n,)))
+        last = np.zeros(n, dtype=np.float64)
+        o = _Adapt(kappa, chunk, tw_first, tw_min, tw_max)
+        code = library().sr_run_batch_adaptive(self._ctx, _ptr(te), C.byref(o), _ptr(last))
+        for b in range(n):
+            self.t_c[b] = self.observables(b).t_c
+        _check(code, "sr_run_batch_adaptive")
+        return last
 
     def reset(self) -> None:
         _check(library().sr_reset(self._ctx), "sr_reset")

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -1965,7 +1966,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   if (n < 1 || !reps) return SR_EINVAL;
   if (p.region_w < 1 || p.region_h < 1) return SR_EINVAL;
   if (p.capacity < 0 || p.max_iters < 0 || p.trace_capacity < 0 || p.threads_per_block < 0 ||
-      p.block_threads < 0 || p.blocks < 0 || p.barrier_timeout_ms < 0)
+      p.blocks < 0 || p.barrier_timeout_ms < 0)
     return SR_EINVAL;
   if (p.lanes_per_region != 0 && p.lanes_per_region != 1 && p.lanes_per_region != 32) return SR_EINVAL;
   if (p.lanes_per_warp < 0 || p.lanes_per_warp > 32 || p.time_arith < 0 || p.time_arith > 2)
@@ -2056,7 +2057,8 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
       if (lanes < 1) lanes = 1;
       if (lanes > 32) lanes = 32;
     }
-    const int soft = p.time_arith == 2 || (p.time_arith == 0 && lanes * 16 * c->num_sms < c->NR);
+    // FP64 unless asked: measured faster than the emulation at every lane count
+    const int soft = p.time_arith == 2;
     c->mode = soft ? 2 : 0;
     c->lanes = lanes;
     int wpb = p.threads_per_block ? (p.threads_per_block + lanes - 1) / lanes : 0;
@@ -2522,6 +2524,169 @@ int sr_eval_softfloat(int op, const double* a, const double* b, double* out, siz
   if (db) cudaFree(db);
   if (dout) cudaFree(dout);
   return rc;
+}
+
+int sr_run_batch_adaptive(sr_ctx* c, const double* t_end, const sr_adapt* opts, double* last_tw) {
+  if (!c || !t_end) return SR_EINVAL;
+  sr_adapt o;
+  std::memset(&o, 0, sizeof o);
+  if (opts) o = *opts;
+  if (o.kappa == 0.0) o.kappa = 8.0;
+  if (o.chunk == 0.0) o.chunk = 1.0;
+  if (o.tw_first == 0.0) o.tw_first = 1.0 / 16.0;
+  if (o.tw_min == 0.0) o.tw_min = std::ldexp(1.0, -10);
+  if (o.tw_max == 0.0) o.tw_max = o.chunk;
+  const double vals[5] = {o.kappa, o.chunk, o.tw_first, o.tw_min, o.tw_max};
+  for (double v : vals)
+    if (!(v > 0.0) || !std::isfinite(v)) return SR_EINVAL;
+  if (o.tw_min > o.tw_max) return SR_EINVAL;
+  const int n = c->nrep;
+  for (int b = 0; b < n; ++b)
+    if (!(t_end[b] >= c->t_c[b]) || !std::isfinite(t_end[b])) return SR_EINVAL;
+  // window length to the nearest power of two, clamped
+  auto pow2 = [&](double v) {
+    double w = std::ldexp(1.0, (int)std::lround(std::log2(v)));
+    if (w < o.tw_min) w = o.tw_min;
+    if (w > o.tw_max) w = o.tw_max;
+    return w;
+  };
+  double* tw = (double*)std::malloc((size_t)n * sizeof(double));
+  double* Tw = (double*)std::malloc((size_t)n * sizeof(double));
+  double* span = (double*)std::malloc((size_t)n * sizeof(double));
+  unsigned long long* c0 = (unsigned long long*)std::malloc((size_t)n * sizeof(unsigned long long));
+  int* nw = (int*)std::malloc((size_t)n * sizeof(int));
+  int rc = SR_OK;
+  if (!tw || !Tw || !span || !c0 || !nw) rc = SR_ENOMEM;
+  if (rc == SR_OK) {
+    for (int b = 0; b < n; ++b) tw[b] = pow2(o.tw_first);
+    // the per-lattice committed counts before the first chunk
+    if (cudaMemcpyAsync(c->h_rs, c->rs, (size_t)n * sizeof(RepStats), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      rc = SR_ECUDA;
+  }
+  while (rc == SR_OK) {
+    bool any = false;
+    for (int b = 0; b < n; ++b) {
+      const double rem = t_end[b] - c->t_c[b];
+      nw[b] = 0;
+      Tw[b] = 1.0;
+      span[b] = 0.0;
+      c0[b] = c->h_rs[b].committed;
+      if (!(rem > 0.0)) continue;
+      const double sp = rem < o.chunk ? rem : o.chunk;
+      double w = tw[b] < sp ? tw[b] : sp;
+      double k = std::floor(sp / w);
+      if (k < 1.0) k = 1.0;
+      if (k > 1e6) k = 1e6;
+      nw[b] = (int)k;
+      Tw[b] = w;
+      span[b] = k * w;
+      any = true;
+    }
+    if (!any) break;
+    rc = run_all(c, Tw, nw);
+    if (rc != SR_OK) break;
+    for (int b = 0; b < n; ++b) {
+      if (nw[b] == 0) continue;
+      const double dc = (double)(c->h_rs[b].committed - c0[b]);
+      const double rho = dc / ((double)c->hdesc[b].NR * span[b]);
+      tw[b] = rho > 0.0 ? pow2(o.kappa / rho) : o.tw_max;
+      if (last_tw) last_tw[b] = Tw[b];
+    }
+  }
+  std::free(tw);
+  std::free(Tw);
+  std::free(span);
+  std::free(c0);
+  std::free(nw);
+  return rc;
+}
+
+int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t_trial,
+                sr_tune* out) {
+  if (!reps || n < 1 || !common || !out) return SR_EINVAL;
+  if (t_trial == 0.0) t_trial = 1.0;
+  if (!(t_trial > 0.0) || !std::isfinite(t_trial)) return SR_EINVAL;
+  std::memset(out, 0, sizeof *out);
+  const int shapes[5][2] = {{16, 16}, {8, 8}, {32, 32}, {16, 8}, {32, 16}};
+  bool ok[5];
+  int n_ok = 0;
+  for (int s = 0; s < 5; ++s) {
+    ok[s] = true;
+    for (int b = 0; b < n; ++b)
+      if (reps[b].L % shapes[s][0] || reps[b].L % shapes[s][1]) ok[s] = false;
+    n_ok += ok[s];
+  }
+  if (n_ok == 0) return SR_EUNSUPPORTED;
+  double* te = (double*)std::malloc((size_t)n * sizeof(double));
+  if (!te) return SR_ENOMEM;
+  // one trial: committed flips per second over [t_trial / 2, t_trial]
+  auto trial = [&](int w, int h, int lpw, double kappa, double* score) -> int {
+    sr_params p = *common;
+    p.region_w = w;
+    p.region_h = h;
+    p.lanes_per_warp = lpw;
+    sr_ctx* c = nullptr;
+    int rc = create_common(&c, reps, n, p);
+    if (rc != SR_OK) return rc;
+    sr_adapt o;
+    std::memset(&o, 0, sizeof o);
+    o.kappa = kappa;
+    o.chunk = t_trial / 4.0;
+    for (int b = 0; b < n; ++b) te[b] = 0.5 * t_trial;
+    rc = sr_run_batch_adaptive(c, te, &o, nullptr);
+    unsigned long long before = 0, after = 0;
+    for (int b = 0; b < n && rc == SR_OK; ++b) before += c->h_rs[b].committed;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int b = 0; b < n; ++b) te[b] = t_trial;
+    if (rc == SR_OK) rc = sr_run_batch_adaptive(c, te, &o, nullptr);
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int b = 0; b < n && rc == SR_OK; ++b) after += c->h_rs[b].committed;
+    sr_destroy(c);
+    *score = dt > 0.0 ? (double)(after - before) / dt : 0.0;
+    out->trials += 1;
+    return rc;
+  };
+  int rc = SR_OK;
+  int bw = 0, bh = 0, blpw = 0;
+  double bk = 8.0, best = -1.0;
+  for (int s = 0; s < 5 && rc == SR_OK; ++s) {
+    if (!ok[s]) continue;
+    double sc = 0.0;
+    rc = trial(shapes[s][0], shapes[s][1], 0, bk, &sc);
+    if (rc == SR_OK && sc > best) {
+      best = sc;
+      bw = shapes[s][0];
+      bh = shapes[s][1];
+    }
+  }
+  const double kappas[2] = {4.0, 16.0};
+  for (int i = 0; i < 2 && rc == SR_OK; ++i) {
+    double sc = 0.0;
+    rc = trial(bw, bh, 0, kappas[i], &sc);
+    if (rc == SR_OK && sc > best) {
+      best = sc;
+      bk = kappas[i];
+    }
+  }
+  const int lpws[3] = {8, 16, 32};
+  for (int i = 0; i < 3 && rc == SR_OK; ++i) {
+    double sc = 0.0;
+    rc = trial(bw, bh, lpws[i], bk, &sc);
+    if (rc == SR_OK && sc > best) {
+      best = sc;
+      blpw = lpws[i];
+    }
+  }
+  std::free(te);
+  if (rc != SR_OK) return rc;
+  out->region_w = bw;
+  out->region_h = bh;
+  out->lanes_per_warp = blpw;
+  out->kappa = bk;
+  out->flips_per_s = best;
+  return SR_OK;
 }
 
 int sr_get_info(sr_ctx* c, int* n_regions, int* frac_bits, uint64_t* P, int* threads_per_block,

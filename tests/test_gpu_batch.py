@@ -137,3 +137,81 @@ def test_batch_reset_and_bad_arguments():
         sr.Batch([dict(L=20)], region=(8, 8))      # 20 is not a multiple of 8
     with pytest.raises(sr.SRError):
         sr.Batch([], region=(8, 8))
+
+
+# ----------------------------------------------------------------- adaptive windows
+def _check_at(batch, b, W, H, t_final, n_windows_min=1):
+    r = batch.replicas[b]
+    ref = oracle.run(r.L, r.J, r.h, r.T, W, H, r.seed, [t_final], init_mode=INIT[r.init],
+                     glauber=(r.rates == "glauber"))
+    assert np.array_equal(batch.spins(b), ref.spins[-1]), f"spins of lattice {b}"
+    i, x, bb, t = batch.carry(b)
+    assert np.array_equal(i, ref.carry_i)
+    assert np.array_equal(x, ref.carry_x)
+    assert np.array_equal(bb, ref.carry_b)
+    assert np.array_equal(t, ref.carry_t)
+    o = batch.observables(b)
+    assert o.committed == int(ref.counts[-1].sum())
+    assert o.windows >= n_windows_min
+
+
+@pytest.mark.parametrize("m", [0, 1])
+def test_adaptive_windows_bit_exact(m):
+    """Window lengths chosen from each lattice's event rate do not change its
+    trajectory; every lattice ends exactly at its own target time."""
+    t_end = [3.0, 2.0, 4.0, 1.5, 2.5, 0.0]
+    with sr.Batch(REPS, region=(8, 8), **MAPS[m]) as batch:
+        last = batch.run_adaptive(t_end, kappa=4.0, chunk=0.5)
+        for b in range(len(REPS)):
+            assert batch.t_c[b] == t_end[b]
+            if t_end[b] > 0:
+                assert last[b] > 0 and last[b] == 2.0 ** round(np.log2(last[b]))
+                _check_at(batch, b, 8, 8, t_end[b])
+        # continue to non-dyadic ends
+        t2 = [3.3, 2.7, 4.0, 1.9, 2.5, 0.7]
+        batch.run_adaptive(t2)
+        for b in range(len(REPS)):
+            assert batch.t_c[b] == t2[b]
+            _check_at(batch, b, 8, 8, t2[b])
+
+
+def test_adaptive_argument_checks():
+    with sr.Batch(REPS[:2], region=(8, 8)) as batch:
+        batch.run_adaptive([1.0, 1.0])
+        with pytest.raises(sr.SRError):
+            batch.run_adaptive([0.5, 2.0])          # before the committed time
+        with pytest.raises(sr.SRError):
+            batch.run_adaptive([2.0, 2.0], kappa=-1.0)
+        with pytest.raises(sr.SRError):
+            batch.run_adaptive([2.0, 2.0], tw_min=1.0, tw_max=0.5)
+
+
+def test_autotune_small_batch():
+    reps = [dict(L=32, T=1.5, h=0.05, seed=31), dict(L=64, T=3.0, h=0.0, seed=32),
+            dict(L=96, T=2.2, h=-0.1, seed=33)]
+    t = sr.autotune(reps, t_trial=0.5)
+    # 96 is not a multiple of 64 but every candidate shape divides 32, 64, 96
+    assert (t.region[0], t.region[1]) in [(16, 16), (8, 8), (32, 32), (16, 8), (32, 16)]
+    assert t.lanes_per_warp in (0, 8, 16, 32)
+    assert t.kappa in (4.0, 8.0, 16.0)
+    assert t.trials == 5 + 2 + 3
+    assert t.flips_per_s > 0
+    with sr.Batch(reps, region=t.region, lanes_per_warp=t.lanes_per_warp) as batch:
+        batch.run_adaptive(1.0, kappa=t.kappa)
+        for b in range(3):
+            _check_at(batch, b, t.region[0], t.region[1], 1.0)
+    with pytest.raises(sr.SRError):
+        sr.autotune([dict(L=36, T=2.0)])              # no candidate shape divides 36
+
+
+def test_batched_workload_sample_bit_exact():
+    """The 256-lattice batched workload (L from 64 to 1024, T in [1, 3.5],
+    h in [-0.2, 0.2]) to t = 0.25 with adaptive windows; a stratified sample
+    of lattices against their oracle runs."""
+    from paper_cs_0405053_gb300 import workloads
+    reps = workloads.batch_replicas()
+    with sr.Batch(reps, region=(16, 16)) as batch:
+        batch.run_adaptive(0.25, kappa=8.0, chunk=0.125)
+        assert np.all(batch.t_c == 0.25)
+        for b in range(0, len(reps), 11):
+            _check_at(batch, b, 16, 16, 0.25)
