@@ -211,6 +211,33 @@ def _batched_vs_plain(args, sr, torch, stream):
     }
 
 
+def _fg_vs_log_n(sr):
+    """f and g of §6 versus log N: L = 64 .. 2048 in 16x16 regions (N = 16 ..
+    16384), T = 3.0, h = 0, T_max = log N / (lambda |boundary|) (Eq. 5.1,
+    lambda = 1, 60 boundary sites); 20 windows of warm-up, 60 measured."""
+    rows = []
+    for L in (64, 128, 256, 512, 1024, 2048):
+        N = (L // RW) ** 2
+        Tw = math.log(N) / 60.0
+        lat = sr.Lattice(L, 1.0, 0.0, 3.0, (RW, RH), seed=7)
+        lat.run_windows(Tw, 20)
+        o0 = lat.observables()
+        t0 = time.perf_counter()
+        lat.run_windows(Tw, 60)
+        dt = time.perf_counter() - t0
+        o = lat.observables()
+        f = lat.window_f(60)
+        g = lat.window_iters(60)
+        lat.close()
+        lg = math.log(N)
+        rows.append({"N": N, "log_N": round(lg, 3), "T_max": round(Tw, 5),
+                     "f_mean": float(f.mean()), "f_max": int(f.max()),
+                     "g_mean": float(g.mean()), "g_max": int(g.max()),
+                     "f_over_log_N": float(f.mean()) / lg, "g_over_log_N": float(g.mean()) / lg,
+                     "flips_per_s": (o.committed - o0.committed) / dt})
+    return rows
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -332,6 +359,7 @@ def run_ours(args):
     hbm_bound_events = HBM_GBS * 1e9 / (HIST_BYTES_PER_BOUNDARY_EVENT * 60 / 256)
     cpu_committed, cpu_dt = _oracle_baseline()
     batch_info = None if args.no_batch else _batched_vs_plain(args, sr, torch, stream)
+    fg_rows = None if args.no_batch else _fg_vs_log_n(sr)
     tw_detail = {}
     for Tw in WINDOWS:
         ms, kms_tw, o, iters = per_tw[Tw][-1]
@@ -368,6 +396,7 @@ def run_ours(args):
                                    "trajectory does not depend on window ends)"},
         "clocks": _clock_summary(clock_path, local),
         "batched": batch_info,
+        "fg_vs_log_N": fg_rows,
         "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)
@@ -409,6 +438,32 @@ def run_profile_case(args):
     return 0
 
 
+def run_profile_batch(args):
+    """A short slice of the batched workload for profilers: the 256 lattices
+    in 32x16 regions (32 region lanes per warp, 16 events per window target),
+    one chunk [0, 1) untimed, then `--windows` chunks of one time unit, each
+    chunk one persistent launch."""
+    import torch
+
+    import paper_cs_0405053_gb300 as sr
+    from paper_cs_0405053_gb300 import workloads
+    torch.cuda.set_device(0)
+    reps = workloads.batch_replicas()
+    bt = sr.Batch(reps, region=(32, 16), lanes_per_warp=32)
+    bt.run_adaptive(1.0, kappa=16.0, chunk=1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt.run_adaptive(1.0 + args.windows, kappa=16.0, chunk=1.0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    obs = [bt.observables(b) for b in range(len(reps))]
+    com = sum(o.committed for o in obs)
+    print(json.dumps({"profile_batch": True, "chunks": args.windows, "s": dt,
+                      "committed_total": com, "launches": obs[0].launches,
+                      "blocks": bt.blocks, "region_slots_per_block": bt.threads_per_block}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,9 +483,13 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
     ap.add_argument("--replay", type=int, default=0,
                     help="checkpoint records per region for incremental replay (0 auto, -1 off)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="run only a short slice of the batched workload (for ncu)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -81,6 +81,12 @@ typedef struct sr_params {
   int replay_records;           /* incremental replay (one lane per region): checkpoints kept per
                                    region of the break points consumed in a pass, so the next pass
                                    restarts after its last unchanged input; 0 = 64, -1 = off */
+  int fresh_steps;              /* 0: each step continues every region's clock and random numbers
+                                   (§5, "Subsequent steps"); 1: the alternate approach of §5:
+                                   at every committed time each region's clock restarts with new
+                                   random numbers (event j of window w: Philox counter
+                                   (j, w, region, 2)); the trajectory then depends on the window
+                                   ends.  One lane per region only (SR_EUNSUPPORTED otherwise) */
   int test_barrier_skip_block;  /* test hook: this block never arrives at a barrier; -1 = off */
   void* stream;                 /* cudaStream_t; NULL = the library creates its own */
 } sr_params;
@@ -110,6 +116,8 @@ typedef struct sr_obs {
   uint64_t breaks;              /* break points processed in every iteration (§5) */
   uint64_t windows;             /* committed windows */
   uint64_t iterations;          /* iterations over all windows */
+  uint64_t sum_f;               /* sum over committed windows of f (§6): the most boundary
+                                   events of a region in an iteration of the window */
   uint32_t last_iters;          /* iterations of the last window (g of §6) */
   uint32_t max_iters_seen;      /* largest g seen */
   uint32_t max_f;               /* largest number of boundary events of one region in one
@@ -285,6 +293,11 @@ int sr_get_trace(sr_ctx* ctx, uint64_t* lens, double* times, uint32_t* sites, si
  * sr_run_window(s) call (at most 4096); returns how many were written or a
  * negative code. */
 int sr_get_window_iters(sr_ctx* ctx, uint32_t* out, size_t n);
+
+/* f of §6 for the same windows: the largest number of boundary events
+ * (events at boundary sites, §5) of any region in any iteration of the
+ * window.  Same conventions as sr_get_window_iters. */
+int sr_get_window_f(sr_ctx* ctx, uint32_t* out, size_t n);
 
 /* Geometry and the fixed-point rate table actually used: P[k] / 2^F is the
  * flip probability of class k (the grid keeps Lambda = sum N_k p_k exact);

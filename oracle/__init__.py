@@ -46,7 +46,8 @@ def build(force: bool = False) -> str:
 class _Params(C.Structure):
     _fields_ = [("L", C.c_int), ("J", C.c_double), ("h", C.c_double), ("T", C.c_double),
                 ("region_w", C.c_int), ("region_h", C.c_int), ("seed", C.c_uint64),
-                ("init_mode", C.c_int), ("glauber", C.c_int), ("debug", C.c_int)]
+                ("init_mode", C.c_int), ("glauber", C.c_int), ("debug", C.c_int),
+                ("fresh_steps", C.c_int)]
 
 
 class _Outputs(C.Structure):
@@ -166,12 +167,16 @@ class RunResult:
 def run(L: int, J: float, h: float, T: float, region_w: int, region_h: int, seed: int,
         t_end: Sequence[float], init_mode: int = INIT_FAIR_COIN,
         init_spins: Optional[np.ndarray] = None, glauber: bool = False, debug: bool = False,
-        keep_spins: bool = True, keep_counts: bool = True, trace_cap: int = 0) -> RunResult:
-    """Run the global time-order simulation from t = 0 through each t_end."""
+        keep_spins: bool = True, keep_counts: bool = True, trace_cap: int = 0,
+        fresh_steps: bool = False) -> RunResult:
+    """Run the global time-order simulation from t = 0 through each t_end.
+    fresh_steps: the alternate step rule of §5 (clocks restart with new
+    random numbers at every t_end but the last)."""
     t_end = np.ascontiguousarray(t_end, dtype=np.float64)
     nw = len(t_end)
     nreg = (L // region_w) * (L // region_h)
-    prm = _Params(L, J, h, T, region_w, region_h, seed, init_mode, int(glauber), int(debug))
+    prm = _Params(L, J, h, T, region_w, region_h, seed, init_mode, int(glauber), int(debug),
+                  int(fresh_steps))
     spins = np.zeros((nw, L, L), dtype=np.int8) if keep_spins else None
     counts = np.zeros((nw, nreg), dtype=np.uint64) if keep_counts else None
     mag = np.zeros(nw, dtype=np.int64)

@@ -223,6 +223,9 @@ typedef struct {
   int init_mode;              /* 0 fair coin (Philox INIT stream), 1 all +1, 2 all -1, 3 given spins */
   int glauber;                /* 0 Metropolis (Eq. 2.2), 1 Glauber (Eq. 2.3) */
   int debug;                  /* check the invariants after every event */
+  int fresh_steps;            /* 0: the carry of §5 "Subsequent steps"; 1: §5 "An alternate
+                                 approach to subsequent steps" -- at every window end all
+                                 clocks restart with new random numbers */
 } orc_params;
 
 /* Caller-owned output buffers; any pointer may be NULL. */
@@ -252,6 +255,9 @@ typedef struct {
   int L, rw, rh, nrx, nry, nreg, F;
   uint64_t P[10];
   uint32_t key[2];
+  int fresh;                  /* the alternate step rule */
+  uint32_t window;            /* index of the running window (alternate rule) */
+  uint64_t* ev0;              /* per-region event index at the window start (alternate rule) */
   int8_t* s;                  /* spins, y*L + x */
   int8_t* cls;                /* class of every site */
   int (*N)[10];               /* per-region class counts */
@@ -295,8 +301,16 @@ static uint64_t region_lambda(const orc_state* st, int r) {
   return lam;
 }
 
+/* The pair (U, V) of region r's pending event.  Carry rule: counter
+ * (i_lo, i_hi, r, 0) for event index i.  Alternate rule: the j-th event of
+ * window w takes counter (j, w, r, 2), numbers no earlier window has used. */
 static void draw(orc_state* st, int r) {
   uint32_t ctr[4] = {(uint32_t)st->ev[r], (uint32_t)(st->ev[r] >> 32), (uint32_t)r, 0u};
+  if (st->fresh) {
+    ctr[0] = (uint32_t)(st->ev[r] - st->ev0[r]);
+    ctr[1] = st->window;
+    ctr[3] = 2u;
+  }
   uint32_t w[4];
   orc_philox4x32_10(ctr, st->key, w);
   uint64_t ku = ((((uint64_t)w[1]) << 32) | w[0]) >> 12;
@@ -431,12 +445,15 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
   orc_rates_fixed(p, st.F, st.P);
   st.key[0] = (uint32_t)prm->seed;
   st.key[1] = (uint32_t)(prm->seed >> 32);
+  st.fresh = prm->fresh_steps != 0;
+  st.window = 0;
   size_t nsite = (size_t)L * L, nreg = (size_t)st.nreg;
   st.s = malloc(nsite);
   st.cls = malloc(nsite);
   st.N = calloc(nreg, sizeof *st.N);
   st.lam = calloc(nreg, 8);
   st.ev = calloc(nreg, 8);
+  st.ev0 = calloc(nreg, 8);
   st.x = calloc(nreg, 8);
   st.kv = calloc(nreg, 8);
   st.b = calloc(nreg, 8);
@@ -449,7 +466,7 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
   int* mark = calloc(nreg, sizeof(int));
   int* touched_regions = calloc(nreg * 3 + 8, sizeof(int));
   int rc = 0;
-  if (!st.s || !st.cls || !st.N || !st.lam || !st.ev || !st.x || !st.kv || !st.b || !st.tl ||
+  if (!st.s || !st.cls || !st.N || !st.lam || !st.ev || !st.ev0 || !st.x || !st.kv || !st.b || !st.tl ||
       !st.tau || !st.heap || !st.hpos || !tie || !chosen || !mark || !touched_regions) {
     rc = -2;
     goto done;
@@ -582,6 +599,22 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
     int_bonds += (double)st.bonds * (te - t_prev);
     t_prev = te;
     record_window(&st, out, w, int_mag, int_bonds);
+    if (st.fresh && w + 1 < n_windows) {
+      /* the alternate rule: wipe the slate at t_c = te; every region's clock
+       * restarts there with the first pair of the next window's numbers
+       * (exponential waiting times are memoryless, so the law is unchanged) */
+      st.window = (uint32_t)(w + 1);
+      for (int r = 0; r < st.nreg; r++) {
+        st.ev0[r] = st.ev[r];
+        draw(&st, r);
+        st.b[r] = 0.0;
+        st.tl[r] = te;
+        st.tau[r] = orc_tau(st.tl[r], st.x[r], st.b[r], st.lam[r], st.F);
+        st.heap[r] = r;
+        st.hpos[r] = r;
+      }
+      for (int i = st.nreg / 2; i >= 0; i--) heap_sift_down(&st, i);
+    }
   }
   for (int r = 0; r < st.nreg; r++) {
     if (out->carry_i) out->carry_i[r] = st.ev[r];
@@ -590,7 +623,8 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
     if (out->carry_t) out->carry_t[r] = st.tl[r];
   }
 done:
-  free(st.s); free(st.cls); free(st.N); free(st.lam); free(st.ev); free(st.x); free(st.kv);
+  free(st.s); free(st.cls); free(st.N); free(st.lam); free(st.ev); free(st.ev0); free(st.x);
+  free(st.kv);
   free(st.b); free(st.tl); free(st.tau); free(st.heap); free(st.hpos);
   free(tie); free(chosen); free(mark); free(touched_regions);
   return rc;

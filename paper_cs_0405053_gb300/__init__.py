@@ -41,7 +41,7 @@ class _Params(C.Structure):
                 ("lanes_per_region", C.c_int), ("lanes_per_warp", C.c_int), ("time_arith", C.c_int),
                 ("threads_per_block", C.c_int), ("blocks", C.c_int),
                 ("barrier_timeout_ms", C.c_int), ("replay_records", C.c_int),
-                ("test_barrier_skip_block", C.c_int),
+                ("fresh_steps", C.c_int), ("test_barrier_skip_block", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -76,7 +76,8 @@ class _Obs(C.Structure):
     _fields_ = [("t_c", C.c_double), ("mag", C.c_int64), ("bonds", C.c_int64), ("m", C.c_double),
                 ("E", C.c_double), ("int_mag", C.c_double), ("int_bonds", C.c_double),
                 ("committed", C.c_uint64), ("generated", C.c_uint64), ("breaks", C.c_uint64),
-                ("windows", C.c_uint64), ("iterations", C.c_uint64), ("last_iters", C.c_uint32),
+                ("windows", C.c_uint64), ("iterations", C.c_uint64), ("sum_f", C.c_uint64),
+                ("last_iters", C.c_uint32),
                 ("max_iters_seen", C.c_uint32), ("max_f", C.c_uint32), ("capacity", C.c_uint32),
                 ("launches", C.c_uint64), ("region_passes", C.c_uint64),
                 ("region_skips", C.c_uint64), ("run_cycles", C.c_uint64),
@@ -97,6 +98,7 @@ class Observables:
     breaks: int
     windows: int
     iterations: int
+    sum_f: int
     last_iters: int
     max_iters_seen: int
     max_f: int
@@ -139,6 +141,7 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_get_carry": (C.c_int, [_P, _P, _P, _P, _P, C.c_size_t]),
             "sr_get_trace": (C.c_int, [_P, _P, _P, _P, C.c_size_t, C.c_size_t]),
             "sr_get_window_iters": (C.c_int, [_P, _P, C.c_size_t]),
+            "sr_get_window_f": (C.c_int, [_P, _P, C.c_size_t]),
             "sr_eval_draws": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint64, C.c_size_t, _P, _P]),
             "sr_get_info": (C.c_int, [_P, _P, _P, _P, _P, _P]),
             "sr_eval_softfloat": (C.c_int, [C.c_int, _P, _P, _P, C.c_size_t]),
@@ -206,7 +209,7 @@ class Lattice:
                  time_arith: int = 0, threads_per_block: int = 0,
                  blocks: int = 0,
                  barrier_timeout_ms: int = 0, replay_records: int = 0,
-                 test_barrier_skip_block: int = -1,
+                 fresh_steps: bool = False, test_barrier_skip_block: int = -1,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
         lib = library()
         if stream is None and use_torch_stream:
@@ -218,7 +221,8 @@ class Lattice:
         prm = _Params(L, J, h, T, region[0], region[1], seed, INIT_MODES[init], RATES[rates],
                       capacity, max_iters, trace_capacity, lanes_per_region, lanes_per_warp,
                       time_arith, threads_per_block, blocks,
-                      barrier_timeout_ms, replay_records, test_barrier_skip_block, stream)
+                      barrier_timeout_ms, replay_records, int(fresh_steps),
+                      test_barrier_skip_block, stream)
         self._ctx = _P()
         _check(lib.sr_create_ex(C.byref(self._ctx), C.byref(prm)), "sr_create_ex")
         n_regions = C.c_int()
@@ -319,19 +323,29 @@ class Lattice:
         return lens, times, sites
 
     def window_iters(self, n: int = 4096) -> np.ndarray:
+        """Iterations g of each of the last n windows of the last run call."""
         out = np.zeros(n, dtype=np.uint32)
         m = library().sr_get_window_iters(self._ctx, _ptr(out), n)
         if m < 0:
             raise SRError(m, "sr_get_window_iters")
         return out[:m]
 
+    def window_f(self, n: int = 4096) -> np.ndarray:
+        """f of §6 (most boundary events of a region in an iteration) of each
+        of the last n windows of the last run call."""
+        out = np.zeros(n, dtype=np.uint32)
+        m = library().sr_get_window_f(self._ctx, _ptr(out), n)
+        if m < 0:
+            raise SRError(m, "sr_get_window_f")
+        return out[:m]
+
 
 def _common_params(region, capacity=0, max_iters=0, lanes_per_region=0, lanes_per_warp=0,
                    time_arith=0, threads_per_block=0, blocks=0, barrier_timeout_ms=0,
-                   replay_records=0, stream=None) -> _Params:
+                   replay_records=0, stream=None, fresh_steps=False) -> _Params:
     return _Params(0, 0.0, 0.0, 0.0, region[0], region[1], 0, 0, 0, capacity, max_iters, 0,
                    lanes_per_region, lanes_per_warp, time_arith, threads_per_block, blocks,
-                   barrier_timeout_ms, replay_records, -1, stream)
+                   barrier_timeout_ms, replay_records, int(fresh_steps), -1, stream)
 
 
 def _replica_array(replicas):
@@ -376,6 +390,7 @@ class Batch:
                  max_iters: int = 0, lanes_per_region: int = 0, lanes_per_warp: int = 0,
                  time_arith: int = 0, threads_per_block: int = 0, blocks: int = 0,
                  barrier_timeout_ms: int = 0, replay_records: int = 0,
+                 fresh_steps: bool = False,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
         lib = library()
         if stream is None and use_torch_stream:
@@ -384,7 +399,7 @@ class Batch:
         self.region = region
         prm = _common_params(region, capacity, max_iters, lanes_per_region, lanes_per_warp,
                              time_arith, threads_per_block, blocks, barrier_timeout_ms,
-                             replay_records, stream)
+                             replay_records, stream, fresh_steps)
         self._arr = arr
         self._ctx = _P()
         _check(lib.sr_create_batch(C.byref(self._ctx), C.cast(arr, C.c_void_p), len(arr),

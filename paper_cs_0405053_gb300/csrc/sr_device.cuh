@@ -71,13 +71,25 @@ __device__ __forceinline__ double neg_log_unit(uint64_t k52) {
 // The pair (U_i, V_i) of event i of a region: U feeds Eq. 3.4 (returned as
 // x = -log U), V feeds the class/site choice (returned as its 52-bit integer
 // kV, V = (2 kV + 1) 2^-53).
-__device__ __forceinline__ void draw_event(unsigned long long i, uint32_t region, uint32_t key0,
-                                           uint32_t key1, double& x, unsigned long long& kv) {
+__device__ __forceinline__ void draw_counter(uint32_t c0, uint32_t c1, uint32_t region, uint32_t tag,
+                                             uint32_t key0, uint32_t key1, double& x,
+                                             unsigned long long& kv) {
   uint32_t w[4];
-  philox4x32_10((uint32_t)i, (uint32_t)(i >> 32), region, 0u, key0, key1, w);
+  philox4x32_10(c0, c1, region, tag, key0, key1, w);
   const unsigned long long ku = ((((unsigned long long)w[1]) << 32) | w[0]) >> 12;
   kv = ((((unsigned long long)w[3]) << 32) | w[2]) >> 12;
   x = neg_log_unit(ku);
+}
+__device__ __forceinline__ void draw_event(unsigned long long i, uint32_t region, uint32_t key0,
+                                           uint32_t key1, double& x, unsigned long long& kv) {
+  draw_counter((uint32_t)i, (uint32_t)(i >> 32), region, 0u, key0, key1, x, kv);
+}
+// The alternate step rule of §5: the j-th event of window w has its own
+// numbers, counter (j, w, region, 2), never used by an earlier window.
+__device__ __forceinline__ void draw_event_fresh(unsigned j, unsigned w, uint32_t region,
+                                                 uint32_t key0, uint32_t key1, double& x,
+                                                 unsigned long long& kv) {
+  draw_counter(j, w, region, 2u, key0, key1, x, kv);
 }
 
 // ---------------------------------------------------------------- time

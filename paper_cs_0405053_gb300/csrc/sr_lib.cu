@@ -57,6 +57,7 @@ struct RepDesc {
   uint32_t key0, key1;          // seed
   int nwin;                     // windows to run in the current launch
   int init_mode;                // SR_INIT_* of sr_reset
+  unsigned w0;                  // windows committed before the current launch
   double t0, Tw;                // committed time at the launch, window length
   unsigned long long P[10];     // p_k on the 2^-F grid
   unsigned long long Rp[10];    // floor((2^64 - 1) / P[k]) (0 when P[k] = 0)
@@ -65,6 +66,7 @@ struct RepDesc {
 // Per-lattice counters.
 struct RepStats {
   unsigned long long committed, generated, breaks, windows, iterations;
+  unsigned long long sum_f;     // sum over committed windows of f (§6)
   unsigned last_iters, max_iters_seen, max_f, max_win_events;
   unsigned windows_done;        // windows committed in the current launch
 };
@@ -111,7 +113,9 @@ struct KParams {
   int rl;                       // region slots per block (the other threads only help fill)
   int lanes;                    // lane mappings: region lanes in each warp
   DevStats* st;
-  uint32_t* win_iters;          // [kWinRing] iterations of each window of lattice 0
+  uint32_t* win_iters;          // [2][kWinRing] iterations g and f of each window of lattice 0
+  uint32_t* curf;               // [2][nrep] f of the running window, by window parity
+  int fresh;                    // the alternate step rule of §5
   int max_iters;
   long long timeout_cycles;
   int skip_block;
@@ -186,38 +190,78 @@ __device__ __noinline__ bool grid_barrier(DevStats* st, long long timeout) {
 // A lane's region: rows in shared memory (stride = threads per block), halos
 // in registers.  Bit x of row y is the spin (1 = up) of site (x, y).
 struct Region {
-  uint32_t* rows;   // rows[y * stride]
-  uint32_t* N;      // N[k * stride]
-  uint32_t* C;      // C[(k * hq + y/4) * stride]: byte y%4 = sites of class k in row y
-  int hq;           // count words per class, (H + 3) / 4
+  uint32_t* rows;              // rows[y * stride]
+  uint32_t* C;                 // C[(k * hq + y/4) * stride]: byte y%4 = sites of class k in row y
+  unsigned long long* PT;      // PT[k * stride] = P_k, PT[(10 + k) * stride] = its reciprocal
+  int cur_rep;                 // lattice whose table PT holds (-1: none)
+  int hq;                      // count words per class, (H + 3) / 4
   int stride;
   int W, H;
-  bool spans_x, spans_y;   // the region covers the whole periodic extent
+  bool spans_x, spans_y;       // the region covers the whole periodic extent
   uint32_t wmask;
   uint32_t hN, hS, hW, hE;
 
   __device__ __forceinline__ uint32_t row(int y) const { return rows[y * stride]; }
+  __device__ __forceinline__ unsigned long long P(int k) const { return PT[k * stride]; }
+  __device__ __forceinline__ unsigned long long Rp(int k) const { return PT[(10 + k) * stride]; }
+
+  // Row y for y in [-2, H + 1]: periodic inside a region spanning the lattice,
+  // else the halo row for y = -1 and y = H (0 beyond, never used).
+  __device__ __forceinline__ uint32_t row_at(int y) const {
+    if (y >= 0 && y < H) return row(y);
+    if (spans_y) return row(y < 0 ? y + H : y - H);
+    return y == -1 ? hN : (y == H ? hS : 0u);
+  }
 
   // Neighbour words of row y: bit x = spin of the up/down/left/right neighbour.
-  __device__ __forceinline__ void nbr_words(int y, uint32_t r, uint32_t& up, uint32_t& dn,
-                                            uint32_t& lf, uint32_t& rt) const {
-    up = (y > 0) ? row(y - 1) : (spans_y ? row(H - 1) : hN);
-    dn = (y < H - 1) ? row(y + 1) : (spans_y ? row(0) : hS);
+  __device__ __forceinline__ void side_words(int y, uint32_t r, uint32_t& lf, uint32_t& rt) const {
     const uint32_t lbit = spans_x ? (r >> (W - 1)) & 1u : (hW >> y) & 1u;
     const uint32_t rbit = spans_x ? (r & 1u) : (hE >> y) & 1u;
     lf = ((r << 1) | lbit) & wmask;
     rt = (r >> 1) | (rbit << (W - 1));
   }
+  __device__ __forceinline__ void nbr_words(int y, uint32_t r, uint32_t& up, uint32_t& dn,
+                                            uint32_t& lf, uint32_t& rt) const {
+    up = row_at(y - 1);
+    dn = row_at(y + 1);
+    side_words(y, r, lf, rt);
+  }
 
-  __device__ __forceinline__ int class_at(int x, int y) const {
-    const uint32_t r = row(y);
-    const int s = (r >> x) & 1;
-    const int up = (y > 0) ? (row(y - 1) >> x) & 1
-                           : (spans_y ? (row(H - 1) >> x) & 1 : (hN >> x) & 1);
-    const int dn = (y < H - 1) ? (row(y + 1) >> x) & 1 : (spans_y ? (row(0) >> x) & 1 : (hS >> x) & 1);
-    const int lf = (x > 0) ? (r >> (x - 1)) & 1 : (spans_x ? (r >> (W - 1)) & 1 : (hW >> y) & 1);
-    const int rt = (x < W - 1) ? (r >> (x + 1)) & 1 : (spans_x ? r & 1 : (hE >> y) & 1);
+  // Class 5*s + n_up of site (x, y) from its row rm and the rows above (ru)
+  // and below (rd); left and right from rm or the side halos.
+  __device__ __forceinline__ int class_in(int x, int y, uint32_t ru, uint32_t rm, uint32_t rd) const {
+    const int s = (rm >> x) & 1;
+    const int up = (ru >> x) & 1, dn = (rd >> x) & 1;
+    const int lf = (x > 0) ? (rm >> (x - 1)) & 1 : (spans_x ? (rm >> (W - 1)) & 1 : (hW >> y) & 1);
+    const int rt = (x < W - 1) ? (rm >> (x + 1)) & 1 : (spans_x ? rm & 1 : (hE >> y) & 1);
     return 5 * s + up + dn + lf + rt;
+  }
+
+  // A site of row y moves from class `from` to class `to` (per-row counts).
+  __device__ __forceinline__ void c_move(int from, int to, int y) const {
+    const uint32_t one = 1u << (8 * (y & 3));
+    atomicAdd(&C[(from * hq + (y >> 2)) * stride], 0u - one);
+    atomicAdd(&C[(to * hq + (y >> 2)) * stride], one);
+  }
+};
+
+// The ten class counts N_k in two registers: 12-bit fields, classes 0-4 in lo
+// and 5-9 in hi (a region has at most 1024 sites).
+struct Counts {
+  unsigned long long lo = 0ull, hi = 0ull;
+  __device__ __forceinline__ unsigned get(int k) const {
+    return (unsigned)(((k < 5 ? lo : hi) >> (12 * (k < 5 ? k : k - 5))) & 0xFFFull);
+  }
+  __device__ __forceinline__ unsigned get_dyn(int k) const { return get(k); }
+  __device__ __forceinline__ void add(int k, unsigned v) {
+    const unsigned long long d = (unsigned long long)v << (12 * (k < 5 ? k : k - 5));
+    if (k < 5) lo += d; else hi += d;
+  }
+  __device__ __forceinline__ void move(int from, int to) {
+    const unsigned long long df = 1ull << (12 * (from < 5 ? from : from - 5));
+    const unsigned long long dt = 1ull << (12 * (to < 5 ? to : to - 5));
+    if (from < 5) lo -= df; else hi -= df;
+    if (to < 5) lo += dt; else hi += dt;
   }
 };
 
@@ -253,18 +297,6 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, unsigned j) {
 
 __device__ __forceinline__ uint32_t eq_count(uint32_t s0, uint32_t s1, uint32_t s2, int n) {
   return ((n & 1) ? s0 : ~s0) & ((n & 2) ? s1 : ~s1) & ((n & 4) ? s2 : ~s2);
-}
-
-// Class change of one site: N_k and Lambda follow (§3: "each spin flip changes
-// the class membership of several atoms").
-__device__ __forceinline__ void move_class(const Region& g, const unsigned long long* P, int from,
-                                           int to, int y, unsigned long long& lam) {
-  g.N[from * g.stride] -= 1u;
-  g.N[to * g.stride] += 1u;
-  const uint32_t one = 1u << (8 * (y & 3));
-  g.C[(from * g.hq + (y >> 2)) * g.stride] -= one;
-  g.C[(to * g.hq + (y >> 2)) * g.stride] += one;
-  lam = lam - P[from] + P[to];
 }
 
 // tau of Eq. 3.4 / 5.6 in integer-emulated doubles (same bits as tau_hat).
@@ -344,7 +376,7 @@ __device__ __forceinline__ unsigned long long class_pos(unsigned long long D, un
 
 // ---------------------------------------------------------------- region pass
 struct Acc {
-  unsigned long long events, breaks, passes, skips;
+  unsigned events, breaks, passes, skips;   // per slot and iteration: well below 2^32
   unsigned fmax, emax;
   bool changed, overflow;
 };
@@ -370,7 +402,7 @@ __device__ __forceinline__ double accrue_any(double b, double tb, double tl, uns
 
 template <int SOFT>
 __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, unsigned cidx,
-                           double t_s, double t_end, Region& g, Acc& acc) {
+                           double t_s, double t_end, unsigned wg, Region& g, Acc& acc) {
   const int W = p.W, H = p.H, NR = p.NR;
   const int wp = n_iter & 1;
   const int rp = wp ^ 1;
@@ -380,18 +412,18 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   g.spans_x = lt.spans_x;
   g.spans_y = lt.spans_y;
 
-  // ---- neighbours (global region indices): d = 0 N, 1 S, 2 W, 3 E
-  const int qN = lt.off + ((ry + lt.NY - 1) % lt.NY) * lt.NX + rx;
-  const int qS = lt.off + ((ry + 1) % lt.NY) * lt.NX + rx;
-  const int qW = lt.off + ry * lt.NX + (rx + lt.NX - 1) % lt.NX;
-  const int qE = lt.off + ry * lt.NX + (rx + 1) % lt.NX;
-  int q[4] = {qN, qS, qW, qE};
-  bool has[4] = {!g.spans_y, !g.spans_y, !g.spans_x, !g.spans_x};
+  // ---- neighbours (global region indices): d = 0 N, 1 S, 2 W, 3 E.  Every
+  // small per-direction array below is indexed by compile-time constants only
+  // (unrolled loops, selects), so it stays in registers.
+  const int q[4] = {lt.off + ((ry + lt.NY - 1) % lt.NY) * lt.NX + rx,
+                    lt.off + ((ry + 1) % lt.NY) * lt.NX + rx,
+                    lt.off + ry * lt.NX + (rx + lt.NX - 1) % lt.NX,
+                    lt.off + ry * lt.NX + (rx + 1) % lt.NX};
+  const bool has[4] = {!g.spans_y, !g.spans_y, !g.spans_x, !g.spans_x};
 
   // ---- a region whose neighbours' lists did not change in the last iteration
   // sees the same input as then, so its output is the same: keep the
   // tentative state and carry the lists over instead of replaying the window
-  // same output as the last iteration: keep the tentative state, carry the lists over
   auto carry_over = [&]() {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -421,43 +453,52 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
 
   // ---- incoming boundary lists: the neighbours' lists of the previous iteration;
   // my N halo is fed by the N neighbour's S list, etc.
+  // per direction: the time of the next entry, and a cursor word holding the
+  // list length (high 16 bits) and the index of the next entry (low 16 bits);
+  // the four positions share one word, a byte each
   const double INF = __longlong_as_double(0x7FF0000000000000ll);
-  const int ein[4] = {1, 0, 3, 2};
-  unsigned len[4], idx[4];
+  unsigned cur[4], npos = 0u;
   double nt[4];
-  unsigned npos[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
+    const int ein = d ^ 1;                 // the neighbour's edge facing me
     // iteration 1: the canonical assumption, no neighbour flips (§5)
-    len[d] = (has[d] && n_iter >= 2) ? __ldcg(&p.hl[((size_t)rp * 4 + ein[d]) * nr + q[d]]) : 0u;
-    idx[d] = 0;
-    if (len[d] > 0) {
-      const size_t a = (((size_t)rp * 4 + ein[d]) * cap) * nr + q[d];
+    const unsigned len = (has[d] && n_iter >= 2) ? __ldcg(&p.hl[((size_t)rp * 4 + ein) * nr + q[d]]) : 0u;
+    cur[d] = len << 16;
+    nt[d] = INF;
+    if (len > 0) {
+      const size_t a = (((size_t)rp * 4 + ein) * cap) * nr + q[d];
       nt[d] = __ldcg(&p.ht[a]);
-      npos[d] = __ldcg(&p.hp[a]);
-    } else {
-      nt[d] = INF;
-      npos[d] = 0;
+      npos |= (unsigned)__ldcg(&p.hp[a]) << (8 * d);
     }
   }
-  auto next_break = [&](long long& tbb, int& db) {   // ties: lower direction first
+  // earliest pending break point; ties go to the lower direction
+  auto next_break = [&](long long& tbb, int& db, unsigned& pos) {
     tbb = __double_as_longlong(nt[0]);
     db = 0;
 #pragma unroll
     for (int d = 1; d < 4; ++d) {
       const long long v = __double_as_longlong(nt[d]);
-      if (v < tbb) { tbb = v; db = d; }
+      if (v < tbb) {
+        tbb = v;
+        db = d;
+      }
     }
+    pos = (npos >> (8 * db)) & 0xFFu;
   };
   auto advance = [&](int db) {
-    const unsigned nidx = idx[db] + 1;
-    idx[db] = nidx;
-    if (nidx < len[db]) {
-      const size_t a = (((size_t)rp * 4 + ein[db]) * cap + nidx) * nr + q[db];
-      nt[db] = __ldcg(&p.ht[a]);
-      npos[db] = __ldcg(&p.hp[a]);
-    } else {
-      nt[db] = INF;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      if (d == db) {
+        const unsigned c = cur[d] + 1u;
+        cur[d] = c;
+        nt[d] = INF;
+        if ((c & 0xFFFFu) < (c >> 16)) {
+          const size_t a = (((size_t)rp * 4 + (d ^ 1)) * cap + (c & 0xFFFFu)) * nr + q[d];
+          nt[d] = __ldcg(&p.ht[a]);
+          npos = (npos & ~(0xFFu << (8 * d))) | ((unsigned)__ldcg(&p.hp[a]) << (8 * d));
+        }
+      }
     }
   };
 
@@ -473,15 +514,16 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     const unsigned nb_total = hdr[0], nb_log = hdr[1];
     long long tbb;
     int db;
+    unsigned pos;
     while (m < nb_log) {
-      next_break(tbb, db);
+      next_break(tbb, db, pos);
       const uint32_t* rec = rec0 + (size_t)m * rwords;
       const long long rt = (long long)(((unsigned long long)rec[1] << 32) | rec[0]);
-      if (tbb != rt || rec[2] != (npos[db] | ((unsigned)db << 8))) break;
+      if (tbb != rt || rec[2] != (pos | ((unsigned)db << 8))) break;
       advance(db);
       ++m;
     }
-    next_break(tbb, db);
+    next_break(tbb, db, pos);
     if (m == nb_total && m == nb_log && tbb == 0x7FF0000000000000ll) {
       carry_over();          // every input is the one the last pass consumed
       return;
@@ -490,6 +532,17 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   const bool resume = m > 0;
   acc.passes += 1;
 
+  // the lattice's rate table and reciprocals, staged in this slot's shared
+  // memory when the slot moves to another lattice
+  if (g.cur_rep != lt.rep) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+      g.PT[k * g.stride] = lt.P[k];
+      g.PT[(10 + k) * g.stride] = lt.Rp[k];
+    }
+    g.cur_rep = lt.rep;
+  }
+
   unsigned long long i;
   double x, b, tl;
   unsigned long long kv;
@@ -497,7 +550,6 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   unsigned bevents = 0;
   int ksig = 0, kbeta = 0;
   Acc128 ssig = {0ull, 0}, sbeta = {0ull, 0};
-  const unsigned long long i_win = p.ci[cidx * nr + r];   // first event of the window
   if (resume) {
     // ---- state after the m-th consumed break of the last pass
     const uint32_t* rec = rec0 + (size_t)(m - 1) * rwords;
@@ -528,37 +580,49 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     g.hS = p.halo[1 * nr + r];
     g.hW = p.halo[2 * nr + r];
     g.hE = p.halo[3 * nr + r];
-    i = i_win;
-    b = p.cb[cidx * nr + r];
-    tl = p.ct[cidx * nr + r];
+    i = p.ci[cidx * nr + r];        // first event of the window
+    // the carry of §5 "Subsequent steps", or (alternate rule) a clock that
+    // restarts at the window start with no hazard accrued
+    b = p.fresh ? 0.0 : p.cb[cidx * nr + r];
+    tl = p.fresh ? t_s : p.ct[cidx * nr + r];
   }
   // presimulated pairs (U, V) of the coming events (§4: the random numbers
   // as a list drawn before use); the pair of event i+1 is loaded one event ahead
   const unsigned long long hi = p.rhi[r];
-  const unsigned long long kmask = (unsigned long long)p.K - 1ull;
-  if (!resume) {
+  const unsigned kmask = (unsigned)p.K - 1u;     // K is a power of two <= 4096
+  // events past the ring are drawn here (alternate rule: numbered from the window start)
+  auto draw_at = [&](unsigned long long ii, double& xx, unsigned long long& kk) {
+    if (p.fresh)
+      draw_event_fresh((unsigned)(ii - p.ci[cidx * nr + r]), wg, (uint32_t)lt.loc, lt.key0,
+                       lt.key1, xx, kk);
+    else
+      draw_event(ii, (uint32_t)lt.loc, lt.key0, lt.key1, xx, kk);
+  };
+  if (!resume && !p.fresh) {
     x = p.cx[cidx * nr + r];
     kv = p.ckv[cidx * nr + r];
   } else if (i < hi) {
-    const size_t a = (size_t)(i & kmask) * nr + r;
+    const size_t a = (size_t)((unsigned)i & kmask) * nr + r;
     x = p.rx[a];
     kv = p.rkv[a];
   } else {
-    draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
+    draw_at(i, x, kv);
   }
   double px = 0.0;
   unsigned long long pkv = 0ull;
   bool pvalid = (i + 1ull) < hi;
   if (pvalid) {
-    const size_t a = (size_t)((i + 1ull) & kmask) * nr + r;
+    const size_t a = (size_t)((unsigned)(i + 1ull) & kmask) * nr + r;
     px = p.rx[a];
     pkv = p.rkv[a];
   }
 
-  // ---- class counts N_k, Lambda, and the region's spin / owned-bond sums
-  unsigned Nk[10], cw[10];
+  // ---- class counts N_k (packed in registers, Counts), the per-row class
+  // counts in shared memory, Lambda, and the region's spin / owned-bond sums
+  Counts N;
+  uint32_t cw[10];
 #pragma unroll
-  for (int k = 0; k < 10; ++k) Nk[k] = cw[k] = 0;
+  for (int k = 0; k < 10; ++k) cw[k] = 0;
   int mag0 = 0, bond0 = 0;
   for (int y = 0; y < H; ++y) {
     const uint32_t rw = g.row(y);
@@ -570,8 +634,8 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     for (int n = 0; n < 5; ++n) {
       const uint32_t e = eq_count(s0, s1, s2, n) & g.wmask;
       const unsigned cu = __popc(e & rw), cd = __popc(e & ~rw);
-      Nk[5 + n] += cu;
-      Nk[n] += cd;
+      N.add(5 + n, cu);
+      N.add(n, cd);
       cw[5 + n] |= cu << sh;
       cw[n] |= cd << sh;
     }
@@ -587,10 +651,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   }
   unsigned long long lam = 0;
 #pragma unroll
-  for (int k = 0; k < 10; ++k) {
-    g.N[k * g.stride] = Nk[k];
-    lam += (unsigned long long)Nk[k] * lt.P[k];
-  }
+  for (int k = 0; k < 10; ++k) lam += (unsigned long long)N.get(k) * g.P(k);
   if (resume) {                      // window-start sums, kept since the first pass
     mag0 = (int)hdr[2];
     bond0 = (int)hdr[3];
@@ -599,12 +660,14 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     hdr[3] = (uint32_t)bond0;
   }
 
-  // own lists: previous lengths for the comparison (§4, statement (c)); on a
-  // resumed pass the entries before the checkpoint are the same as last time
-  unsigned plen[4];
+  // own lists: on a resumed pass the entries before the checkpoint are the
+  // same as last time.  The previous lengths (for the comparison of §4,
+  // statement (c)) are read where they are needed.
+  auto plen = [&](int e) -> unsigned {
+    return n_iter >= 2 ? __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]) : 0u;
+  };
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    plen[e] = (has[e] && n_iter >= 2) ? __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]) : 0u;
     if (resume && has[e]) {
       for (unsigned j = 0; j < olen[e]; ++j) {
         const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
@@ -616,20 +679,19 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   }
 
   bool changed = false, overflow = false;
-  unsigned long long events = 0, brk = 0;
+  unsigned events = 0, brk = 0;
   unsigned nrec = m, nbt = m;           // checkpoint records kept, breaks consumed
   // window integrals of the observables in fixed point (times as multiples of 2^-frac)
   const int frac = 62 - (int)((((unsigned long long)__double_as_longlong(t_end)) >> 52) - 1022);
-  const uint32_t gx0 = (uint32_t)(rx * W), gy0 = (uint32_t)(ry * H);
   const long long tend_b = __double_as_longlong(t_end);
 
   // times are >= 0, so their bit patterns order like their values
   double tau = tau_any<SOFT>(tl, x, b, lam, p);
   for (;;) {
-    // earliest pending break point
     long long tbb;
     int db;
-    next_break(tbb, db);
+    unsigned bpos;
+    next_break(tbb, db, bpos);
     const double tb = __longlong_as_double(tbb);
     const long long taub = __double_as_longlong(tau);
 
@@ -637,64 +699,110 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       // ---- own event at tau, unless it falls past the window (§5: tau_m < t_c + T_max)
       if (!(taub < tend_b)) break;
       // class k* of Eqs. 3.5-3.6, exactly: P = V*Lambda*2^(53+F) as a 128-bit
-      // integer (q53, rem); class k is chosen when P <= A(k) * 2^53.
+      // integer (q53, rem); class k is chosen when P <= A(k) * 2^53.  All ten
+      // prefix sums are formed (no early exit), so lanes do not diverge.
       const unsigned long long mV = 2ull * kv + 1ull;
       const unsigned long long plo = mV * lam, phi = __umul64hi(mV, lam);
       const unsigned long long q53 = (phi << 11) | (plo >> 53);
       const bool exact = (plo & ((1ull << 53) - 1ull)) == 0ull;
-      unsigned long long A = 0, Aprev = 0;
-      int ks = 9;
+      unsigned long long A = 0, Aprev = 0, A8 = 0;
+      int ks = -1;
+#pragma unroll
       for (int k = 0; k < 10; ++k) {
-        Aprev = A;
-        A += (unsigned long long)g.N[k * g.stride] * lt.P[k];
-        if (q53 < A || (q53 == A && exact)) { ks = k; break; }
+        const unsigned long long Ak = A + (unsigned long long)N.get(k) * g.P(k);
+        const bool hit = ks < 0 && (q53 < Ak || (q53 == Ak && exact));
+        if (hit) {
+          ks = k;
+          Aprev = A;
+        }
+        if (k == 8) A8 = Ak;
+        A = Ak;
+      }
+      if (ks < 0) {          // not reachable for V < 1; the last class as a guard
+        ks = 9;
+        Aprev = A8;
       }
       // position within the class, Eqs. 3.7-3.8: floor((V*Lambda - A(k*-1)) / p_k*)
-      const unsigned Nks = g.N[ks * g.stride];
-      unsigned long long j = class_pos(q53 - Aprev, lt.P[ks], lt.Rp[ks]);
+      const unsigned Nks = N.get_dyn(ks);
+      unsigned long long j = class_pos(q53 - Aprev, g.P(ks), g.Rp(ks));
       if (j >= Nks) j = Nks - 1;
-      unsigned jj = (unsigned)j;
-      // the jj-th class-k* site in row-major order (linear order of §3, Phase 3):
+      // the j-th class-k* site in row-major order (linear order of §3, Phase 3):
       // the row from the per-row counts of class k*, then the site in that row
+      unsigned jj = (unsigned)j;
+      int fy = 0;
+      {
+        const uint32_t* Ck = g.C + (ks * g.hq) * g.stride;
+        unsigned base = 0, jr = 0;
+        uint32_t wsel = 0;
+        int qsel = -1;
+        for (int qd = 0; qd < g.hq; ++qd) {
+          const uint32_t w = Ck[qd * g.stride];
+          const unsigned s4 = __vsadu4(w, 0u);        // sites of class k* in these 4 rows
+          const bool hit = qsel < 0 && jj < base + s4;
+          if (hit) {
+            qsel = qd;
+            wsel = w;
+            jr = jj - base;
+          }
+          base += s4;
+        }
+        const unsigned c0 = wsel & 0xFFu, c1 = (wsel >> 8) & 0xFFu, c2 = (wsel >> 16) & 0xFFu;
+        const unsigned u1 = jr >= c0, u2 = jr >= c0 + c1, u3 = jr >= c0 + c1 + c2;
+        jj = jr - (u1 ? c0 : 0u) - (u2 ? c1 : 0u) - (u3 ? c2 : 0u);
+        fy = 4 * qsel + (int)(u1 + u2 + u3);
+      }
+      // ---- the rows around fy (periodic, or the halo rows at the region edge)
+      const uint32_t rM = g.row(fy);
+      const uint32_t rU = g.row_at(fy - 1), rD = g.row_at(fy + 1);
       const int sp = ks >= 5;
       const int nn = ks - 5 * sp;
-      int fx = 0, fy = 0;
-      for (int qd = 0; qd < g.hq; ++qd) {
-        const uint32_t w = g.C[(ks * g.hq + qd) * g.stride];
-        const unsigned s4 = __vsadu4(w, 0u);        // sites of class k* in these 4 rows
-        if (jj < s4) {
-          int u = 0;
-          for (; u < 3; ++u) {
-            const unsigned cy = (w >> (8 * u)) & 0xFFu;
-            if (jj < cy) break;
-            jj -= cy;
-          }
-          fy = 4 * qd + u;
-          break;
-        }
-        jj -= s4;
-      }
+      int fx;
       {
-        const uint32_t rw = g.row(fy);
-        uint32_t up, dn, lf, rt, s0, s1, s2;
-        g.nbr_words(fy, rw, up, dn, lf, rt);
-        add4(up, dn, lf, rt, s0, s1, s2);
-        fx = nth_set_bit(eq_count(s0, s1, s2, nn) & (sp ? rw : ~rw) & g.wmask, jj);
+        uint32_t lf, rt, s0, s1, s2;
+        g.side_words(fy, rM, lf, rt);
+        add4(rU, rD, lf, rt, s0, s1, s2);
+        fx = nth_set_bit(eq_count(s0, s1, s2, nn) & (sp ? rM : ~rM) & g.wmask, jj);
       }
       // ---- flip (fx, fy); classes of the site and its in-region neighbours
-      const int cv = g.class_at(fx, fy);
+      // (taken before the flip); E, W, S, N neighbours
+      const bool vE = fx < W - 1 || g.spans_x, vW = fx > 0 || g.spans_x;
+      const bool vS = fy < H - 1 || g.spans_y, vN = fy > 0 || g.spans_y;
+      const int xE = (fx + 1 == W) ? 0 : fx + 1, xW = (fx == 0) ? W - 1 : fx - 1;
+      const int yS = (fy + 1 == H) ? 0 : fy + 1, yN = (fy == 0) ? H - 1 : fy - 1;
+      const int cv = g.class_in(fx, fy, rU, rM, rD);
+      const int cE = g.class_in(xE, fy, rU, rM, rD);
+      const int cW = g.class_in(xW, fy, rU, rM, rD);
+      const int cS = g.class_in(fx, yS, rM, rD, g.row_at(fy + 2));
+      const int cN = g.class_in(fx, yN, g.row_at(fy - 2), rU, rM);
       const int s_old = cv >= 5;
       const int nup = cv - 5 * s_old;
       const int dnb = s_old ? -1 : 1;          // change of the neighbours' up count
-      int nbx[4], nby[4], nbc[4], nnb = 0;
-      if (fx < W - 1 || g.spans_x) { nbx[nnb] = (fx + 1 == W) ? 0 : fx + 1; nby[nnb] = fy; ++nnb; }
-      if (fx > 0 || g.spans_x) { nbx[nnb] = (fx == 0) ? W - 1 : fx - 1; nby[nnb] = fy; ++nnb; }
-      if (fy < H - 1 || g.spans_y) { nbx[nnb] = fx; nby[nnb] = (fy + 1 == H) ? 0 : fy + 1; ++nnb; }
-      if (fy > 0 || g.spans_y) { nbx[nnb] = fx; nby[nnb] = (fy == 0) ? H - 1 : fy - 1; ++nnb; }
-      for (int a = 0; a < nnb; ++a) nbc[a] = g.class_at(nbx[a], nby[a]);
-      g.rows[fy * g.stride] ^= (1u << fx);
-      move_class(g, lt.P, cv, cv + (s_old ? -5 : 5), fy, lam);
-      for (int a = 0; a < nnb; ++a) move_class(g, lt.P, nbc[a], nbc[a] + dnb, nby[a], lam);
+      g.rows[fy * g.stride] = rM ^ (1u << fx);
+      // Lambda's change, in wrap-around unsigned arithmetic (exact at the end)
+      unsigned long long dl = g.P(cv + (s_old ? -5 : 5)) - g.P(cv);
+      N.move(cv, cv + (s_old ? -5 : 5));
+      g.c_move(cv, cv + (s_old ? -5 : 5), fy);
+      if (vE) {
+        dl += g.P(cE + dnb) - g.P(cE);
+        N.move(cE, cE + dnb);
+        g.c_move(cE, cE + dnb, fy);
+      }
+      if (vW) {
+        dl += g.P(cW + dnb) - g.P(cW);
+        N.move(cW, cW + dnb);
+        g.c_move(cW, cW + dnb, fy);
+      }
+      if (vS) {
+        dl += g.P(cS + dnb) - g.P(cS);
+        N.move(cS, cS + dnb);
+        g.c_move(cS, cS + dnb, yS);
+      }
+      if (vN) {
+        dl += g.P(cN + dnb) - g.P(cN);
+        N.move(cN, cN + dnb);
+        g.c_move(cN, cN + dnb, yN);
+      }
+      lam += dl;
 
       // observables: dM = 2 sig, dBonds = 4 beta (Eq. 2.1 book-keeping)
       const int sig = s_old ? -1 : 1;
@@ -726,7 +834,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
             const size_t a = (((size_t)wp * 4 + e) * cap + n) * nr + r;
             p.ht[a] = tau;
             p.hp[a] = (uint8_t)pos;
-            if (n < plen[e]) {
+            if (n < plen(e)) {
               const size_t pa = (((size_t)rp * 4 + e) * cap + n) * nr + r;
               if (__double_as_longlong(__ldcg(&p.ht[pa])) != __double_as_longlong(tau) ||
                   __ldcg(&p.hp[pa]) != (uint8_t)pos)
@@ -741,7 +849,8 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       if (boundary) ++bevents;
       if (p.tcap > 0 && i < (unsigned long long)p.tcap) {
         p.trt[(size_t)r * p.tcap + i] = tau;
-        p.trs[(size_t)r * p.tcap + i] = (gy0 + fy) * (uint32_t)lt.L + gx0 + fx;
+        p.trs[(size_t)r * p.tcap + i] =
+            ((uint32_t)(ry * H) + fy) * (uint32_t)lt.L + (uint32_t)(rx * W) + fx;
       }
       ++events;
       if (overflow) break;
@@ -753,11 +862,11 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
         x = px;
         kv = pkv;
       } else {
-        draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
+        draw_at(i, x, kv);
       }
       pvalid = (i + 1ull) < hi;
       if (pvalid) {
-        const size_t a = (size_t)((i + 1ull) & kmask) * nr + r;
+        const size_t a = (size_t)((unsigned)(i + 1ull) & kmask) * nr + r;
         px = p.rx[a];
         pkv = p.rkv[a];
       }
@@ -765,7 +874,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       // ---- break point: a neighbour flip at tb < tau (§5, Eqs. 5.2-5.6)
       b = accrue_any<SOFT>(b, tb, tl, lam, p);
       tl = tb;
-      const unsigned pos = npos[db];
+      const unsigned pos = bpos;
       int ux, uy, up_now;
       if (db == 0) { g.hN ^= 1u << pos; up_now = (g.hN >> pos) & 1; ux = pos; uy = 0; }
       else if (db == 1) { g.hS ^= 1u << pos; up_now = (g.hS >> pos) & 1; ux = pos; uy = H - 1; }
@@ -773,8 +882,11 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       else { g.hE ^= 1u << pos; up_now = (g.hE >> pos) & 1; ux = W - 1; uy = pos; }
       // class of the adjacent site after the change; before it, its up count
       // differed by one
-      const int cu_new = g.class_at(ux, uy);
-      move_class(g, lt.P, cu_new + (up_now ? -1 : 1), cu_new, uy, lam);
+      const int cu_new = g.class_in(ux, uy, g.row_at(uy - 1), g.row(uy), g.row_at(uy + 1));
+      const int cu_old = cu_new + (up_now ? -1 : 1);
+      lam += g.P(cu_new) - g.P(cu_old);
+      N.move(cu_old, cu_new);
+      g.c_move(cu_old, cu_new, uy);
       // checkpoint after this break point, for the next pass's replay
       if (nrec < (unsigned)p.CB) {
         uint32_t* rec = rec0 + (size_t)nrec * rwords;
@@ -816,7 +928,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     if (has[e]) {
-      if (olen[e] != plen[e]) changed = true;
+      if (olen[e] != plen(e)) changed = true;
       p.hl[((size_t)wp * 4 + e) * nr + r] = olen[e];
     }
   }
@@ -846,7 +958,10 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
 
   acc.events += events;
   acc.breaks += brk;
-  if ((unsigned)(i - i_win) > acc.emax) acc.emax = (unsigned)(i - i_win);
+  {
+    const unsigned long long i_win = p.ci[cidx * nr + r];   // first event of the window
+    if ((unsigned)(i - i_win) > acc.emax) acc.emax = (unsigned)(i - i_win);
+  }
   if (bevents > acc.fmax) acc.fmax = bevents;
   acc.changed |= changed || overflow;
   acc.overflow |= overflow;
@@ -1313,12 +1428,17 @@ __device__ void fill_ring(const KParams& p) {
       const Lat lt = lat_of(p, r);
       const unsigned long long lo = __ldcg(&p.ci[(size_t)p.rcidx[r] * nr + r]);
       const unsigned long long hi_old = p.rhi[r];
-      const unsigned long long from = hi_old > lo ? hi_old : lo;
+      // the alternate step rule starts every window on new numbers: refill all
+      const unsigned long long from = (hi_old > lo && !p.fresh) ? hi_old : lo;
       const unsigned long long to = lo + (unsigned long long)p.K;
+      const unsigned wg = p.reps[lt.rep].w0 + p.rwin[r];
       for (unsigned long long i = from + threadIdx.x; i < to; i += blockDim.x) {
         double x;
         unsigned long long kv;
-        draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
+        if (p.fresh)
+          draw_event_fresh((unsigned)(i - lo), wg, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
+        else
+          draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
         const size_t a = (size_t)(i & kmask) * nr + r;
         p.rx[a] = x;
         p.rkv[a] = kv;
@@ -1362,10 +1482,14 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
   const int sfirst = is_slot ? (int)(blockIdx.x * p.rl + slot) : p.NR;
   Region g;
   const int stride = p.rl;
-  g.rows = smem + (LANES && is_slot ? slot : 0);
-  g.N = smem + p.H * stride + (LANES && is_slot ? slot : 0);
   g.hq = (p.H + 3) / 4;
-  g.C = smem + (p.H + 10) * stride + (LANES && is_slot ? slot : 0);
+  g.rows = smem + (LANES && is_slot ? slot : 0);
+  g.C = smem + p.H * stride + (LANES && is_slot ? slot : 0);
+  {
+    const int pt_words = ((p.H + 10 * g.hq) * stride + 1) & ~1;   // 8-byte aligned table
+    g.PT = reinterpret_cast<unsigned long long*>(smem + pt_words) + (LANES && is_slot ? slot : 0);
+  }
+  g.cur_rep = -1;
   g.stride = stride;
   g.W = p.W;
   g.H = p.H;
@@ -1416,7 +1540,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
   for (;;) {
     const unsigned fslot = giter % 3u;
     ++giter;
-    Acc acc = {0ull, 0ull, 0ull, 0ull, 0u, 0u, false, false};
+    Acc acc = {0u, 0u, 0u, 0u, 0u, 0u, false, false};
     const long long c0 = clock64();
     for (int r = sfirst; r < p.NR; r += sstride) {
       const int b = (int)__ldg(&p.rrep[r]);
@@ -1427,19 +1551,22 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
       const double t_end = __dadd_rn(t_s, d->Tw);
       const unsigned cidx = p.rcidx[r];
       const int n = (int)p.rn[r];
-      Acc ra = {0ull, 0ull, 0ull, 0ull, 0u, 0u, false, false};
+      Acc ra = {0u, 0u, 0u, 0u, 0u, 0u, false, false};
+      const unsigned wg = d->w0 + p.rwin[r];
       if (MODE == 0)
-        run_region<0>(p, lt, r, n, cidx, t_s, t_end, g, ra);
+        run_region<0>(p, lt, r, n, cidx, t_s, t_end, wg, g, ra);
       else if (MODE == 2)
-        run_region<1>(p, lt, r, n, cidx, t_s, t_end, g, ra);
+        run_region<1>(p, lt, r, n, cidx, t_s, t_end, wg, g, ra);
       else
         run_region_warp(p, lt, r, n, cidx, t_s, t_end, ra);
       if (reporter) {
         RepStats* rs = p.rs + b;
+        // f of §6: the most boundary events of a region in an iteration
+        if (ra.fmax) atomicMax(&p.curf[(p.rwin[r] & 1u) * p.nrep + b], ra.fmax);
         if (ra.changed) atomicOr(&p.rflags[fslot * p.nrep + b], 1u);
         if (ra.overflow) atomicOr(&st->status, ST_CAPACITY);
-        if (ra.events) atomicAdd(&rs->generated, ra.events);
-        if (ra.breaks) atomicAdd(&rs->breaks, ra.breaks);
+        if (ra.events) atomicAdd(&rs->generated, (unsigned long long)ra.events);
+        if (ra.breaks) atomicAdd(&rs->breaks, (unsigned long long)ra.breaks);
         if (ra.fmax) atomicMax(&rs->max_f, ra.fmax);
         if (ra.emax) atomicMax(&rs->max_win_events, ra.emax);
         acc.passes += ra.passes;
@@ -1448,8 +1575,8 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
     }
     run_cyc += (unsigned long long)(clock64() - c0);
     if (reporter) {
-      if (acc.passes) atomicAdd(&st->region_passes, acc.passes);
-      if (acc.skips) atomicAdd(&st->region_skips, acc.skips);
+      if (acc.passes) atomicAdd(&st->region_passes, (unsigned long long)acc.passes);
+      if (acc.skips) atomicAdd(&st->region_skips, (unsigned long long)acc.skips);
     }
     if (!grid_barrier(st, p.timeout_cycles)) return;
     if (*(volatile unsigned*)&st->status & (ST_CAPACITY | ST_NOT_CONVERGED)) return;
@@ -1487,7 +1614,14 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
             rs->last_iters = n;
             if (n > rs->max_iters_seen) rs->max_iters_seen = n;
             rs->windows_done = w + 1u;
-            if (b == 0) p.win_iters[w % kWinRing] = n;
+            // f of this window; its parity slot is next written in window w + 2
+            const unsigned fw = p.curf[(w & 1u) * p.nrep + b];
+            p.curf[(w & 1u) * p.nrep + b] = 0u;
+            rs->sum_f += fw;
+            if (b == 0) {
+              p.win_iters[w % kWinRing] = n;
+              p.win_iters[kWinRing + w % kWinRing] = fw;
+            }
             if (w + 1u == (unsigned)d->nwin) atomicSub(&st->active, 1u);
           }
         } else if ((int)n >= p.max_iters) {
@@ -1692,6 +1826,7 @@ struct sr_ctx {
   sr_replica* reps;             // [nrep] their parameters
   RepDesc* hdesc;               // [nrep] host copy of the descriptors
   double* t_c;                  // [nrep] committed time of each lattice
+  unsigned* wins;               // [nrep] committed windows of each lattice
   int NR, F, Lmax;
   double scale;
   cudaStream_t stream;
@@ -1705,7 +1840,7 @@ struct sr_ctx {
   uint8_t *rcidx, *rfill;
   uint32_t *rn, *rwin;
   double* rts;
-  uint32_t *rows, *halo, *hl, *trs, *win_iters, *log, *loghdr;
+  uint32_t *rows, *halo, *hl, *trs, *win_iters, *log, *loghdr, *curf;
   uint8_t* chg;
   int CB;
   unsigned long long *ci, *ckv, *rkv, *rhi;
@@ -1731,7 +1866,7 @@ struct sr_ctx {
 
 namespace {
 
-constexpr int kMaxCap = 1 << 16;
+constexpr int kMaxCap = 1 << 15;   // list cursors hold lengths in 16 bits
 
 int bitlen(long long v) {
   int b = 0;
@@ -1803,6 +1938,8 @@ KParams make_params(const sr_ctx* c) {
   k.lanes = c->lanes;
   k.st = c->st;
   k.win_iters = c->win_iters;
+  k.fresh = c->prm.fresh_steps ? 1 : 0;
+  k.curf = c->curf;
   k.max_iters = c->prm.max_iters;
   k.timeout_cycles = (long long)c->prm.barrier_timeout_ms * (long long)c->clock_khz;
   k.skip_block = c->prm.test_barrier_skip_block;
@@ -1832,12 +1969,14 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SR_OK : SR_ECUDA; }
 // Shared memory of a lane-mapping block: per region slot, H spin rows, ten
 // class counts and ten class-by-row count groups of ceil(H/4) words.
 size_t lane_smem_bytes(int H, int slots) {
-  return (size_t)(H + 10 + 10 * ((H + 3) / 4)) * (size_t)slots * sizeof(uint32_t);
+  const size_t words = ((size_t)(H + 10 * ((H + 3) / 4)) * (size_t)slots + 1) & ~(size_t)1;
+  return (words + 40 * (size_t)slots) * sizeof(uint32_t);
 }
 
-// Allow a kernel more than the default 48 KB of dynamic shared memory.
+// Allow a kernel `bytes` of dynamic shared memory (beyond the default 48 KB,
+// which also counts the kernel's static shared memory, an opt-in is needed).
 bool allow_smem(const void* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return true;
+  if (bytes <= 32 * 1024) return true;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
@@ -1868,6 +2007,7 @@ int init_state(sr_ctx* c, int rep, const int8_t* dev_spins) {
     if (rep >= 0 && b != rep) continue;
     if (cudaMemsetAsync(c->rs + b, 0, sizeof(RepStats), c->stream) != cudaSuccess) return SR_ECUDA;
     c->t_c[b] = 0.0;
+    c->wins[b] = 0u;
   }
   if (rep < 0 && cudaMemsetAsync(c->st, 0, sizeof(DevStats), c->stream) != cudaSuccess) return SR_ECUDA;
   c->last_nwin = 0;
@@ -1881,12 +2021,14 @@ int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
     c->hdesc[b].t0 = c->t_c[b];
     c->hdesc[b].Tw = Tw[b];
     c->hdesc[b].nwin = nwin[b];
+    c->hdesc[b].w0 = c->wins[b];
   }
   int rc = upload_desc(c);
   if (rc != SR_OK) return rc;
   KParams k = make_params(c);
   if (cudaMemsetAsync(c->st, 0, offsetof(DevStats, region_passes), c->stream) != cudaSuccess ||
-      cudaMemsetAsync(c->rflags, 0, 3 * (size_t)c->nrep * sizeof(uint32_t), c->stream) != cudaSuccess)
+      cudaMemsetAsync(c->rflags, 0, 3 * (size_t)c->nrep * sizeof(uint32_t), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->curf, 0, 2 * (size_t)c->nrep * sizeof(uint32_t), c->stream) != cudaSuccess)
     return SR_ECUDA;
   void* args[] = {&k};
   const void* fn = c->mode == 1 ? (const void*)relax_kernel<1>
@@ -1935,7 +2077,7 @@ int set_ring(sr_ctx* c, int K) {
 }
 
 void free_all(sr_ctx* c) {
-  void* dev[] = {c->rows, c->halo, c->hl, c->trs, c->win_iters, c->ci, c->ckv, c->cx, c->cb,
+  void* dev[] = {c->rows, c->halo, c->hl, c->trs, c->win_iters, c->curf, c->ci, c->ckv, c->cx, c->cb,
                  c->ct, c->cim, c->cib, c->ht, c->trt, c->hp, c->st, c->obs_i, c->obs_f, c->stage,
                  c->rx, c->rkv, c->rhi, c->chg, c->log, c->loghdr, c->desc, c->rs, c->rrep,
                  c->rflags, c->rcidx, c->rfill, c->rn, c->rwin, c->rts};
@@ -1949,6 +2091,7 @@ void free_all(sr_ctx* c) {
   std::free(c->reps);
   std::free(c->hdesc);
   std::free(c->t_c);
+  std::free(c->wins);
 }
 
 int check_replica(const sr_replica& r, int W, int H) {
@@ -1971,6 +2114,8 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   if (p.lanes_per_region != 0 && p.lanes_per_region != 1 && p.lanes_per_region != 32) return SR_EINVAL;
   if (p.lanes_per_warp < 0 || p.lanes_per_warp > 32 || p.time_arith < 0 || p.time_arith > 2)
     return SR_EINVAL;
+  if (p.fresh_steps != 0 && p.fresh_steps != 1) return SR_EINVAL;
+  if (p.fresh_steps && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
   if (p.region_w > 32 || p.region_h > 32) return SR_EUNSUPPORTED;
   for (int b = 0; b < n; ++b) {
     const int rc = check_replica(reps[b], p.region_w, p.region_h);
@@ -1985,7 +2130,8 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   c->reps = (sr_replica*)std::calloc((size_t)n, sizeof(sr_replica));
   c->hdesc = (RepDesc*)std::calloc((size_t)n, sizeof(RepDesc));
   c->t_c = (double*)std::calloc((size_t)n, sizeof(double));
-  if (!c->reps || !c->hdesc || !c->t_c) {
+  c->wins = (unsigned*)std::calloc((size_t)n, sizeof(unsigned));
+  if (!c->reps || !c->hdesc || !c->t_c || !c->wins) {
     free_all(c);
     std::free(c);
     return SR_ENOMEM;
@@ -2105,7 +2251,8 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   rc |= dalloc(&c->cib, 2 * nr);
   rc |= dalloc(&c->hl, 2 * 4 * nr);
   rc |= dalloc(&c->st, 1);
-  rc |= dalloc(&c->win_iters, kWinRing);
+  rc |= dalloc(&c->win_iters, 2 * (size_t)kWinRing);
+  rc |= dalloc(&c->curf, 2 * (size_t)n);
   rc |= dalloc(&c->obs_i, 2);
   rc |= dalloc(&c->obs_f, 2);
   rc |= dalloc(&c->stage, (size_t)c->Lmax * c->Lmax);
@@ -2190,6 +2337,7 @@ int run_all(sr_ctx* c, const double* Tw, const int* nwin) {
     for (int b = 0; b < c->nrep; ++b) {
       const int done = (int)c->h_rs[b].windows_done;
       for (int w = 0; w < done; ++w) c->t_c[b] = c->t_c[b] + Tw[b];
+      c->wins[b] += (unsigned)done;
       left[b] -= done;
       total_left += left[b];
       if (b == 0) c->last_nwin += done;
@@ -2247,6 +2395,7 @@ int observables_of(sr_ctx* c, int b, sr_obs* out) {
   out->breaks = rs.breaks;
   out->windows = rs.windows;
   out->iterations = rs.iterations;
+  out->sum_f = rs.sum_f;
   out->last_iters = rs.last_iters;
   out->max_iters_seen = rs.max_iters_seen;
   out->max_f = rs.max_f;
@@ -2301,6 +2450,32 @@ int carry_of(sr_ctx* c, int b, uint64_t* index, double* x, double* bb, double* t
   if (db) cudaFree(db);
   if (dt) cudaFree(dt);
   return rc;
+}
+
+// The last n entries of row `which` (0 iterations, 1 f) of the per-window ring.
+int window_ring(sr_ctx* c, int which, uint32_t* out, size_t n) {
+  if (!c || !out) return SR_EINVAL;
+  const int have = c->last_nwin < kWinRing ? c->last_nwin : kWinRing;
+  const int m = (int)n < have ? (int)n : have;
+  if (m <= 0) return 0;
+  uint32_t* tmp = (uint32_t*)std::malloc(kWinRing * sizeof(uint32_t));
+  if (!tmp) return SR_ENOMEM;
+  if (cudaMemcpyAsync(tmp, c->win_iters + (size_t)which * kWinRing, kWinRing * sizeof(uint32_t),
+                      cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    std::free(tmp);
+    return SR_ECUDA;
+  }
+  // window w of the last launch is at w; a retried call (capacity growth)
+  // restarts at 0, so the last m entries of the final launch are the last windows
+  const int last_launch = (int)c->h_rs[0].windows_done;
+  for (int i = 0; i < m; ++i) {
+    const int w = last_launch - m + i;
+    out[i] = tmp[((w % kWinRing) + kWinRing) % kWinRing];
+  }
+  std::free(tmp);
+  return m;
 }
 
 }  // namespace
@@ -2464,29 +2639,9 @@ int sr_get_trace(sr_ctx* c, uint64_t* lens, double* times, uint32_t* sites, size
   return cuda_rc(cudaStreamSynchronize(c->stream));
 }
 
-int sr_get_window_iters(sr_ctx* c, uint32_t* out, size_t n) {
-  if (!c || !out) return SR_EINVAL;
-  const int have = c->last_nwin < kWinRing ? c->last_nwin : kWinRing;
-  const int m = (int)n < have ? (int)n : have;
-  if (m <= 0) return 0;
-  uint32_t* tmp = (uint32_t*)std::malloc(kWinRing * sizeof(uint32_t));
-  if (!tmp) return SR_ENOMEM;
-  if (cudaMemcpyAsync(tmp, c->win_iters, kWinRing * sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                      c->stream) != cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess) {
-    std::free(tmp);
-    return SR_ECUDA;
-  }
-  // window w of the last launch is at w; a retried call (capacity growth)
-  // restarts at 0, so the last m entries of the final launch are the last windows
-  const int last_launch = (int)c->h_rs[0].windows_done;
-  for (int i = 0; i < m; ++i) {
-    const int w = last_launch - m + i;
-    out[i] = tmp[((w % kWinRing) + kWinRing) % kWinRing];
-  }
-  std::free(tmp);
-  return m;
-}
+int sr_get_window_iters(sr_ctx* c, uint32_t* out, size_t n) { return window_ring(c, 0, out, n); }
+
+int sr_get_window_f(sr_ctx* c, uint32_t* out, size_t n) { return window_ring(c, 1, out, n); }
 
 int sr_eval_draws(uint64_t seed, uint32_t region, uint64_t i0, size_t n, double* x, uint64_t* kV) {
   if (n == 0) return SR_OK;
@@ -2767,6 +2922,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   RepDesc hd;
   std::memset(&hd, 0, sizeof hd);
   double t_c = 0.0;
+  unsigned wins = 0u;
   sr_ctx c;
   std::memset(&c, 0, sizeof c);
   c.prm.L = L;
@@ -2779,6 +2935,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.reps = &rp;
   c.hdesc = &hd;
   c.t_c = &t_c;
+  c.wins = &wins;
   c.F = 63 - bitlen((long long)region_w * region_h);
   c.scale = std::ldexp(1.0, -c.F);
   hd.L = L;
@@ -2811,7 +2968,8 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   probe.take<unsigned long long>((size_t)kNoallocRing * nr);  // ring V
   probe.take<unsigned long long>(nr);             // ring ends
   probe.take<DevStats>(1);
-  probe.take<uint32_t>(kWinRing);
+  probe.take<uint32_t>(2 * (size_t)kWinRing);
+  probe.take<uint32_t>(2);                        // f of the running window
   probe.take<RepDesc>(1);                         // lattice descriptor and counters
   probe.take<RepStats>(1);
   probe.take<uint32_t>(3);                        // convergence flags
@@ -2846,7 +3004,8 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.rkv = cv.take<unsigned long long>((size_t)kNoallocRing * nr);
   c.rhi = cv.take<unsigned long long>(nr);
   c.st = cv.take<DevStats>(1);
-  c.win_iters = cv.take<uint32_t>(kWinRing);
+  c.win_iters = cv.take<uint32_t>(2 * (size_t)kWinRing);
+  c.curf = cv.take<uint32_t>(2);
   c.desc = cv.take<RepDesc>(1);
   c.rs = cv.take<RepStats>(1);
   c.rflags = cv.take<uint32_t>(3);
@@ -2899,7 +3058,8 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   hd.nwin = n_windows;
   if (cudaMemcpyAsync(c.desc, &hd, sizeof hd, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
       cudaMemsetAsync(c.st, 0, offsetof(DevStats, region_passes), c.stream) != cudaSuccess ||
-      cudaMemsetAsync(c.rflags, 0, 3 * sizeof(uint32_t), c.stream) != cudaSuccess)
+      cudaMemsetAsync(c.rflags, 0, 3 * sizeof(uint32_t), c.stream) != cudaSuccess ||
+      cudaMemsetAsync(c.curf, 0, 2 * sizeof(uint32_t), c.stream) != cudaSuccess)
     return SR_ECUDA;
   KParams k = make_params(&c);
   void* args[] = {&k};
