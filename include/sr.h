@@ -87,6 +87,10 @@ typedef struct sr_params {
                                    random numbers (event j of window w: Philox counter
                                    (j, w, region, 2)); the trajectory then depends on the window
                                    ends.  One lane per region only (SR_EUNSUPPORTED otherwise) */
+  int score;                    /* 1: also keep, per region, the committed events by class and
+                                   the integrals of N_k dt (the statistics of the path's score
+                                   function, see sr_score); one lane per region, no incremental
+                                   replay (SR_EUNSUPPORTED with a warp per region) */
   int test_barrier_skip_block;  /* test hook: this block never arrives at a barrier; -1 = off */
   void* stream;                 /* cudaStream_t; NULL = the library creates its own */
 } sr_params;
@@ -241,6 +245,39 @@ typedef struct sr_tune {
 } sr_tune;
 int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t_trial,
                 sr_tune* out);
+
+/* ---- score function (differentiation) ----
+ * A path of the chain of §3 on [0, t_c] has log-likelihood
+ *   log L = sum over events of log p_k(event) - integral of sum_k N_k p_k dt
+ * (k the class of the flipped site before the flip, N_k the class counts).
+ * Its derivative, the score S = d log L / d theta for theta = (beta, h, J)
+ * with beta = 1/T, gives unbiased gradients of expectations: d E[A] / d theta
+ * = E[A S] for any A of the path (plus A's own explicit dependence).  Score
+ * mode (sr_params.score) keeps per region, for the committed path, C_k (events
+ * by class) and I_k (the integral of N_k dt; exact 128-bit fixed point within a
+ * window, accumulated over windows in double).  The paper has no counterpart. */
+
+/* S[b][0..2] = d log L / d(beta, h, J) of each lattice b's committed path:
+ * sum_k C_k d log p_k - sum_k I_k d p_k, with d log p_k of Metropolis
+ * (0 where p_k = 1) or Glauber rates at the lattice's (J, h, T).  out: host,
+ * 3 * n doubles.  Blocks.  Errors: SR_EINVAL, SR_EUNSUPPORTED (not score
+ * mode), SR_ECUDA. */
+int sr_score(sr_ctx* ctx, double* out);
+
+/* The statistics themselves for lattice `replica`, summed over its regions:
+ * counts[k] = C_k, occupancy[k] = I_k (host arrays of 10; either may be NULL). */
+int sr_score_stats(sr_ctx* ctx, int replica, uint64_t* counts, double* occupancy);
+
+/* Backward of n replicas' time averages through their scores, on device
+ * arrays (row-major, caller-owned): A [n][m] the averages, gA [n][m] the
+ * gradient arriving at them, S [n][nq] the scores, E [n][m][nq] the averages'
+ * explicit derivatives (may be NULL).  Writes G [n][nq]:
+ * G[i][q] = sum_j gA[i][j] ((A[i][j] - base_ij) S[i][q] + E[i][j][q]),
+ * base_ij = the mean of A[.][j] over the other replicas (a control variate;
+ * it keeps the estimate unbiased since E[S] = 0).  Runs on `stream`, blocks.
+ * Errors: SR_EINVAL, SR_ENOMEM, SR_ECUDA. */
+int sr_score_grad(int n, int m, int nq, const double* A, const double* gA, const double* S,
+                  const double* E, double* G, void* stream);
 
 /* Observables of lattice `replica` (0 <= replica < n).  Errors: SR_EINVAL,
  * SR_ECUDA. */

@@ -57,7 +57,8 @@ class _Outputs(C.Structure):
                 ("carry_t", C.c_void_p),
                 ("trace_cap", C.c_int64), ("trace_len", C.c_int64),
                 ("tr_region", C.c_void_p), ("tr_index", C.c_void_p), ("tr_time", C.c_void_p),
-                ("tr_site", C.c_void_p), ("debug_failures", C.c_int64)]
+                ("tr_site", C.c_void_p), ("debug_failures", C.c_int64),
+                ("ev_class", C.c_void_p), ("occupancy", C.c_void_p)]
 
 
 _lib = None
@@ -162,6 +163,41 @@ class RunResult:
     tr_time: Optional[np.ndarray]
     tr_site: Optional[np.ndarray]
     debug_failures: int
+    ev_class: np.ndarray               # [n_regions, 10] uint64 events by class before the flip
+    occupancy: np.ndarray              # [n_regions, 10] float64 integral of N_k dt
+
+
+def score_tables(J: float, h: float, T: float, glauber: bool = False):
+    """d log p_k / d theta and d p_k / d theta for theta = (beta, h, J), beta =
+    1/T, for the ten classes k = 5*[s=+1] + n_up (Eqs. 2.1-2.3): the flip of
+    class k changes the energy by dE = 2 s (J (2 n_up - 4) + h).  Metropolis
+    p = min(1, exp(-beta dE)) has d log p = -d(beta dE) where dE > 0 and 0 where
+    dE <= 0 (p = 1 there); Glauber p = e / (1 + e), e = exp(-beta dE), has
+    d log p = -(1 - p) d(beta dE).  Returns (dlogp, dp), each [3, 10]."""
+    beta = 1.0 / T
+    dlogp = np.zeros((3, 10))
+    dp = np.zeros((3, 10))
+    p = rates(J, h, T, glauber)
+    for k in range(10):
+        s = 1.0 if k >= 5 else -1.0
+        nb = 2.0 * (k % 5) - 4.0
+        dE = 2.0 * s * (J * nb + h)
+        d_bdE = np.array([dE, beta * 2.0 * s, beta * 2.0 * s * nb])   # d(beta dE)/d(beta, h, J)
+        if glauber:
+            dlogp[:, k] = -(1.0 - p[k]) * d_bdE
+        elif dE > 0.0:
+            dlogp[:, k] = -d_bdE
+        dp[:, k] = p[k] * dlogp[:, k]
+    return dlogp, dp
+
+
+def score(r: "RunResult", J: float, h: float, T: float, glauber: bool = False) -> np.ndarray:
+    """The score d log L / d(beta, h, J) of the simulated path: the sum over
+    events of d log p_k minus the integral of sum_k N_k dp_k / dtheta."""
+    dlogp, dp = score_tables(J, h, T, glauber)
+    c = r.ev_class.sum(axis=0).astype(np.float64)
+    occ = r.occupancy.sum(axis=0)
+    return dlogp @ c - dp @ occ
 
 
 def run(L: int, J: float, h: float, T: float, region_w: int, region_h: int, seed: int,
@@ -195,9 +231,12 @@ def run(L: int, J: float, h: float, T: float, region_w: int, region_h: int, seed
     if init_spins is not None:
         init = np.ascontiguousarray(init_spins, dtype=np.int8).reshape(L * L)
         prm.init_mode = INIT_GIVEN
+    evc = np.zeros((nreg, 10), dtype=np.uint64)
+    occ = np.zeros((nreg, 10), dtype=np.float64)
     out = _Outputs(_ptr(spins), _ptr(counts), _ptr(mag), _ptr(bonds), _ptr(int_mag),
                    _ptr(int_bonds), _ptr(ci), _ptr(cx), _ptr(cb), _ptr(ct),
-                   trace_cap, 0, _ptr(trr), _ptr(tri), _ptr(trt), _ptr(trs), 0)
+                   trace_cap, 0, _ptr(trr), _ptr(tri), _ptr(trt), _ptr(trs), 0,
+                   _ptr(evc), _ptr(occ))
     rc = lib().orc_run(C.byref(prm), _ptr(init), nw, _ptr(t_end), C.byref(out))
     if rc != 0:
         raise ValueError(f"oracle run failed with code {rc}")
@@ -206,4 +245,4 @@ def run(L: int, J: float, h: float, T: float, region_w: int, region_h: int, seed
                      int(out.trace_len),
                      trr[:n] if trr is not None else None, tri[:n] if tri is not None else None,
                      trt[:n] if trt is not None else None, trs[:n] if trs is not None else None,
-                     int(out.debug_failures))
+                     int(out.debug_failures), evc, occ)

@@ -249,6 +249,11 @@ typedef struct {
   double* tr_time;
   uint32_t* tr_site;          /* global site index y*L + x */
   int64_t debug_failures;     /* written: invariant violations seen */
+  /* the path's sufficient statistics for its score function (log-likelihood
+   * sum_events log p_k - integral sum_k N_k p_k dt, §3 rates): */
+  uint64_t* ev_class;         /* [n_regions][10] committed events by the class of the flipped
+                                 site before its flip */
+  double* occupancy;          /* [n_regions][10] integral of N_k over [0, t_end[last]] */
 } orc_outputs;
 
 typedef struct {
@@ -271,6 +276,9 @@ typedef struct {
   int* heap;                  /* binary min-heap of regions keyed by (tau, region) */
   int* hpos;
   int64_t mag, bonds;
+  double* tseg;               /* per region: time of its last class change (occupancy) */
+  double (*occ)[10];          /* per region: integral of N_k dt so far */
+  uint64_t (*evc)[10];        /* per region: events by class */
 } orc_state;
 
 static int site_region(const orc_state* st, int site) {
@@ -454,6 +462,9 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
   st.lam = calloc(nreg, 8);
   st.ev = calloc(nreg, 8);
   st.ev0 = calloc(nreg, 8);
+  st.tseg = calloc(nreg, 8);
+  st.occ = calloc(nreg, sizeof *st.occ);
+  st.evc = calloc(nreg, sizeof *st.evc);
   st.x = calloc(nreg, 8);
   st.kv = calloc(nreg, 8);
   st.b = calloc(nreg, 8);
@@ -466,7 +477,8 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
   int* mark = calloc(nreg, sizeof(int));
   int* touched_regions = calloc(nreg * 3 + 8, sizeof(int));
   int rc = 0;
-  if (!st.s || !st.cls || !st.N || !st.lam || !st.ev || !st.ev0 || !st.x || !st.kv || !st.b || !st.tl ||
+  if (!st.s || !st.cls || !st.N || !st.lam || !st.ev || !st.ev0 || !st.tseg || !st.occ ||
+      !st.evc || !st.x || !st.kv || !st.b || !st.tl ||
       !st.tau || !st.heap || !st.hpos || !tie || !chosen || !mark || !touched_regions) {
     rc = -2;
     goto done;
@@ -551,6 +563,15 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
         }
       }
       for (int j = 0; j < nt; j++) mark[tie[j]] = 2;   /* own events reset b below */
+      /* occupancy integrals of every region whose classes change at t */
+      for (int a = 0; a < ntr; a++) {
+        int q = touched_regions[a];
+        for (int k = 0; k < 10; k++) st.occ[q][k] += (double)st.N[q][k] * (t - st.tseg[q]);
+        st.tseg[q] = t;
+      }
+      /* events by the class of the flipped site, before any flip at t */
+      for (int j = 0; j < nt; j++)
+        if (chosen[j] >= 0) st.evc[tie[j]][st.cls[chosen[j]]] += 1;
       for (int a = 0; a < ntr; a++) {
         int q = touched_regions[a];
         if (mark[q] == 1) {
@@ -598,6 +619,10 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
     int_mag += (double)st.mag * (te - t_prev);
     int_bonds += (double)st.bonds * (te - t_prev);
     t_prev = te;
+    for (int r = 0; r < st.nreg; r++) {
+      for (int k = 0; k < 10; k++) st.occ[r][k] += (double)st.N[r][k] * (te - st.tseg[r]);
+      st.tseg[r] = te;
+    }
     record_window(&st, out, w, int_mag, int_bonds);
     if (st.fresh && w + 1 < n_windows) {
       /* the alternate rule: wipe the slate at t_c = te; every region's clock
@@ -617,13 +642,18 @@ ORC_EXPORT int orc_run(const orc_params* prm, const int8_t* init_spins, int n_wi
     }
   }
   for (int r = 0; r < st.nreg; r++) {
+    for (int k = 0; k < 10; k++) {
+      if (out->ev_class) out->ev_class[(size_t)r * 10 + k] = st.evc[r][k];
+      if (out->occupancy) out->occupancy[(size_t)r * 10 + k] = st.occ[r][k];
+    }
     if (out->carry_i) out->carry_i[r] = st.ev[r];
     if (out->carry_x) out->carry_x[r] = st.x[r];
     if (out->carry_b) out->carry_b[r] = st.b[r];
     if (out->carry_t) out->carry_t[r] = st.tl[r];
   }
 done:
-  free(st.s); free(st.cls); free(st.N); free(st.lam); free(st.ev); free(st.ev0); free(st.x);
+  free(st.s); free(st.cls); free(st.N); free(st.lam); free(st.ev); free(st.ev0); free(st.tseg);
+  free(st.occ); free(st.evc); free(st.x);
   free(st.kv);
   free(st.b); free(st.tl); free(st.tau); free(st.heap); free(st.hpos);
   free(tie); free(chosen); free(mark); free(touched_regions);

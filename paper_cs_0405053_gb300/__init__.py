@@ -41,7 +41,8 @@ class _Params(C.Structure):
                 ("lanes_per_region", C.c_int), ("lanes_per_warp", C.c_int), ("time_arith", C.c_int),
                 ("threads_per_block", C.c_int), ("blocks", C.c_int),
                 ("barrier_timeout_ms", C.c_int), ("replay_records", C.c_int),
-                ("fresh_steps", C.c_int), ("test_barrier_skip_block", C.c_int),
+                ("fresh_steps", C.c_int), ("score", C.c_int),
+                ("test_barrier_skip_block", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -152,6 +153,9 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_get_spins_replica": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
             "sr_get_carry_replica": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_size_t]),
             "sr_run_batch_adaptive": (C.c_int, [_P, _P, C.POINTER(_Adapt), _P]),
+            "sr_score": (C.c_int, [_P, _P]),
+            "sr_score_stats": (C.c_int, [_P, C.c_int, _P, _P]),
+            "sr_score_grad": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]),
             "sr_autotune": (C.c_int, [_P, C.c_int, C.POINTER(_Params), C.c_double,
                                       C.POINTER(_Tune)]),
         }
@@ -209,7 +213,8 @@ class Lattice:
                  time_arith: int = 0, threads_per_block: int = 0,
                  blocks: int = 0,
                  barrier_timeout_ms: int = 0, replay_records: int = 0,
-                 fresh_steps: bool = False, test_barrier_skip_block: int = -1,
+                 fresh_steps: bool = False, score: bool = False,
+                 test_barrier_skip_block: int = -1,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
         lib = library()
         if stream is None and use_torch_stream:
@@ -221,7 +226,7 @@ class Lattice:
         prm = _Params(L, J, h, T, region[0], region[1], seed, INIT_MODES[init], RATES[rates],
                       capacity, max_iters, trace_capacity, lanes_per_region, lanes_per_warp,
                       time_arith, threads_per_block, blocks,
-                      barrier_timeout_ms, replay_records, int(fresh_steps),
+                      barrier_timeout_ms, replay_records, int(fresh_steps), int(score),
                       test_barrier_skip_block, stream)
         self._ctx = _P()
         _check(lib.sr_create_ex(C.byref(self._ctx), C.byref(prm)), "sr_create_ex")
@@ -330,6 +335,19 @@ class Lattice:
             raise SRError(m, "sr_get_window_iters")
         return out[:m]
 
+    def score(self) -> np.ndarray:
+        """d log L / d(beta, h, J) of the committed path (score mode)."""
+        out = np.zeros(3, dtype=np.float64)
+        _check(library().sr_score(self._ctx, _ptr(out)), "sr_score")
+        return out
+
+    def score_stats(self):
+        """(C_k, I_k): committed events by class and integrals of N_k dt."""
+        c = np.zeros(10, dtype=np.uint64)
+        occ = np.zeros(10, dtype=np.float64)
+        _check(library().sr_score_stats(self._ctx, 0, _ptr(c), _ptr(occ)), "sr_score_stats")
+        return c, occ
+
     def window_f(self, n: int = 4096) -> np.ndarray:
         """f of §6 (most boundary events of a region in an iteration) of each
         of the last n windows of the last run call."""
@@ -342,10 +360,10 @@ class Lattice:
 
 def _common_params(region, capacity=0, max_iters=0, lanes_per_region=0, lanes_per_warp=0,
                    time_arith=0, threads_per_block=0, blocks=0, barrier_timeout_ms=0,
-                   replay_records=0, stream=None, fresh_steps=False) -> _Params:
+                   replay_records=0, stream=None, fresh_steps=False, score=False) -> _Params:
     return _Params(0, 0.0, 0.0, 0.0, region[0], region[1], 0, 0, 0, capacity, max_iters, 0,
                    lanes_per_region, lanes_per_warp, time_arith, threads_per_block, blocks,
-                   barrier_timeout_ms, replay_records, int(fresh_steps), -1, stream)
+                   barrier_timeout_ms, replay_records, int(fresh_steps), int(score), -1, stream)
 
 
 def _replica_array(replicas):
@@ -390,7 +408,7 @@ class Batch:
                  max_iters: int = 0, lanes_per_region: int = 0, lanes_per_warp: int = 0,
                  time_arith: int = 0, threads_per_block: int = 0, blocks: int = 0,
                  barrier_timeout_ms: int = 0, replay_records: int = 0,
-                 fresh_steps: bool = False,
+                 fresh_steps: bool = False, score: bool = False,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
         lib = library()
         if stream is None and use_torch_stream:
@@ -399,7 +417,7 @@ class Batch:
         self.region = region
         prm = _common_params(region, capacity, max_iters, lanes_per_region, lanes_per_warp,
                              time_arith, threads_per_block, blocks, barrier_timeout_ms,
-                             replay_records, stream, fresh_steps)
+                             replay_records, stream, fresh_steps, score)
         self._arr = arr
         self._ctx = _P()
         _check(lib.sr_create_batch(C.byref(self._ctx), C.cast(arr, C.c_void_p), len(arr),
@@ -472,6 +490,18 @@ class Batch:
         _check(library().sr_get_spins_replica(self._ctx, b, _ptr(out), out.size),
                "sr_get_spins_replica")
         return out
+
+    def score(self) -> np.ndarray:
+        """[n, 3]: d log L / d(beta, h, J) of every lattice's committed path."""
+        out = np.zeros((len(self.replicas), 3), dtype=np.float64)
+        _check(library().sr_score(self._ctx, _ptr(out)), "sr_score")
+        return out
+
+    def score_stats(self, b: int):
+        c = np.zeros(10, dtype=np.uint64)
+        occ = np.zeros(10, dtype=np.float64)
+        _check(library().sr_score_stats(self._ctx, b, _ptr(c), _ptr(occ)), "sr_score_stats")
+        return c, occ
 
     def carry(self, b: int):
         r = self.replicas[b]

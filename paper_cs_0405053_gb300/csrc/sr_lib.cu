@@ -94,6 +94,10 @@ struct KParams {
   double* cb;                   // [2][NR]      integral of Lambda since the last event
   double* ct;                   // [2][NR]      time up to which cb is taken
   double* cim;                  // [2][NR]      integral over time of the region's spin sum
+  // path statistics of the score function (score mode): committed events by
+  // the class of the flipped site before the flip, and the integral of N_k dt
+  unsigned long long* sc;       // [2][10][NR]
+  double* si;                   // [2][10][NR]
   double* cib;                  // [2][NR]      integral over time of the region's owned bonds
   double* ht;                   // [2][4][cap][NR] boundary history: times
   uint8_t* hp;                  // [2][4][cap][NR] boundary history: positions along the edge
@@ -116,6 +120,7 @@ struct KParams {
   uint32_t* win_iters;          // [2][kWinRing] iterations g and f of each window of lattice 0
   uint32_t* curf;               // [2][nrep] f of the running window, by window parity
   int fresh;                    // the alternate step rule of §5
+  int score;                    // accumulate the path statistics sc / si
   int max_iters;
   long long timeout_cycles;
   int skip_block;
@@ -193,6 +198,10 @@ struct Region {
   uint32_t* rows;              // rows[y * stride]
   uint32_t* C;                 // C[(k * hq + y/4) * stride]: byte y%4 = sites of class k in row y
   unsigned long long* PT;      // PT[k * stride] = P_k, PT[(10 + k) * stride] = its reciprocal
+  // score mode: per class the window's event count SX[k * stride] and the
+  // window's occupancy sum as a 128-bit fixed-point number,
+  // SX[(10 + 2k) * stride] (low word) and SX[(11 + 2k) * stride] (high word)
+  unsigned long long* SX;
   int cur_rep;                 // lattice whose table PT holds (-1: none)
   int hq;                      // count words per class, (H + 3) / 4
   int stride;
@@ -235,6 +244,27 @@ struct Region {
     const int lf = (x > 0) ? (rm >> (x - 1)) & 1 : (spans_x ? (rm >> (W - 1)) & 1 : (hW >> y) & 1);
     const int rt = (x < W - 1) ? (rm >> (x + 1)) & 1 : (spans_x ? rm & 1 : (hE >> y) & 1);
     return 5 * s + up + dn + lf + rt;
+  }
+
+  // Score mode: a site leaves class `from` and joins `to` at fixed-point time
+  // tf.  The occupancy integral of class k over the window is
+  // N_k(end) t_end - N_k(start) t_start + sum(times of departures from k)
+  // - sum(times of arrivals in k); the sums are kept here.
+  __device__ __forceinline__ void occ_add(int k, unsigned long long tf, bool minus) const {
+    unsigned long long& lo = SX[(10 + 2 * k) * stride];
+    unsigned long long& hi = SX[(11 + 2 * k) * stride];
+    if (minus) {
+      hi -= (lo < tf) ? 1ull : 0ull;
+      lo -= tf;
+    } else {
+      const unsigned long long n = lo + tf;
+      hi += (n < lo) ? 1ull : 0ull;
+      lo = n;
+    }
+  }
+  __device__ __forceinline__ void occ_move(int from, int to, unsigned long long tf) const {
+    occ_add(from, tf, false);
+    occ_add(to, tf, true);
   }
 
   // A site of row y moves from class `from` to class `to` (per-row counts).
@@ -684,6 +714,18 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   // window integrals of the observables in fixed point (times as multiples of 2^-frac)
   const int frac = 62 - (int)((((unsigned long long)__double_as_longlong(t_end)) >> 52) - 1022);
   const long long tend_b = __double_as_longlong(t_end);
+  if (p.score) {
+    // the window's occupancy sums start at -N_k(t_s) t_s, its event counts at 0
+    const unsigned long long tf0 = to_fixed(t_s, frac);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+      const unsigned long long nk = N.get(k);
+      const unsigned long long plo = nk * tf0, phi = __umul64hi(nk, tf0);
+      g.SX[k * g.stride] = 0ull;
+      g.SX[(10 + 2 * k) * g.stride] = 0ull - plo;
+      g.SX[(11 + 2 * k) * g.stride] = 0ull - phi - (plo != 0ull ? 1ull : 0ull);
+    }
+  }
 
   // times are >= 0, so their bit patterns order like their values
   double tau = tau_any<SOFT>(tl, x, b, lam, p);
@@ -699,28 +741,21 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       // ---- own event at tau, unless it falls past the window (§5: tau_m < t_c + T_max)
       if (!(taub < tend_b)) break;
       // class k* of Eqs. 3.5-3.6, exactly: P = V*Lambda*2^(53+F) as a 128-bit
-      // integer (q53, rem); class k is chosen when P <= A(k) * 2^53.  All ten
-      // prefix sums are formed (no early exit), so lanes do not diverge.
+      // integer (q53, rem); class k is chosen when P <= A(k) * 2^53 (the scan
+      // stops there: measured faster than a full branch-free scan)
       const unsigned long long mV = 2ull * kv + 1ull;
       const unsigned long long plo = mV * lam, phi = __umul64hi(mV, lam);
       const unsigned long long q53 = (phi << 11) | (plo >> 53);
       const bool exact = (plo & ((1ull << 53) - 1ull)) == 0ull;
-      unsigned long long A = 0, Aprev = 0, A8 = 0;
-      int ks = -1;
-#pragma unroll
+      unsigned long long A = 0, Aprev = 0;
+      int ks = 9;
       for (int k = 0; k < 10; ++k) {
-        const unsigned long long Ak = A + (unsigned long long)N.get(k) * g.P(k);
-        const bool hit = ks < 0 && (q53 < Ak || (q53 == Ak && exact));
-        if (hit) {
+        Aprev = A;
+        A += (unsigned long long)N.get_dyn(k) * g.P(k);
+        if (q53 < A || (q53 == A && exact)) {
           ks = k;
-          Aprev = A;
+          break;
         }
-        if (k == 8) A8 = Ak;
-        A = Ak;
-      }
-      if (ks < 0) {          // not reachable for V < 1; the last class as a guard
-        ks = 9;
-        Aprev = A8;
       }
       // position within the class, Eqs. 3.7-3.8: floor((V*Lambda - A(k*-1)) / p_k*)
       const unsigned Nks = N.get_dyn(ks);
@@ -738,11 +773,11 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
         for (int qd = 0; qd < g.hq; ++qd) {
           const uint32_t w = Ck[qd * g.stride];
           const unsigned s4 = __vsadu4(w, 0u);        // sites of class k* in these 4 rows
-          const bool hit = qsel < 0 && jj < base + s4;
-          if (hit) {
+          if (jj < base + s4) {
             qsel = qd;
             wsel = w;
             jr = jj - base;
+            break;
           }
           base += s4;
         }
@@ -809,6 +844,14 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       const int beta = sig * (nup - 2);
       {
         const unsigned long long tfix = to_fixed(tau, frac);
+        if (p.score) {                 // score statistics of the event and its class moves
+          g.SX[cv * g.stride] += 1ull;
+          g.occ_move(cv, cv + (s_old ? -5 : 5), tfix);
+          if (vE) g.occ_move(cE, cE + dnb, tfix);
+          if (vW) g.occ_move(cW, cW + dnb, tfix);
+          if (vS) g.occ_move(cS, cS + dnb, tfix);
+          if (vN) g.occ_move(cN, cN + dnb, tfix);
+        }
         ksig += sig;
         ssig.add(sig, tfix);
         kbeta += beta;
@@ -887,6 +930,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       lam += g.P(cu_new) - g.P(cu_old);
       N.move(cu_old, cu_new);
       g.c_move(cu_old, cu_new, uy);
+      if (p.score) g.occ_move(cu_old, cu_new, to_fixed(tb, frac));
       // checkpoint after this break point, for the next pass's replay
       if (nrec < (unsigned)p.CB) {
         uint32_t* rec = rec0 + (size_t)nrec * rwords;
@@ -954,6 +998,22 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     const double ib = __dadd_rn(__dmul_rn((double)bond0, span), __dmul_rn(4.0, ub.value(frac)));
     p.cim[tc * nr + r] = __dadd_rn(p.cim[cidx * nr + r], im);
     p.cib[tc * nr + r] = __dadd_rn(p.cib[cidx * nr + r], ib);
+  }
+  if (p.score) {
+    // close the window's occupancy sums with N_k(t_end) t_end; add to the totals
+    const unsigned long long tfe = to_fixed(t_end, frac);
+    for (int k = 0; k < 10; ++k) {
+      const unsigned long long nk = N.get_dyn(k);
+      const unsigned long long plo = nk * tfe, phi = __umul64hi(nk, tfe);
+      const unsigned long long lo = g.SX[(10 + 2 * k) * g.stride];
+      const unsigned long long hi = g.SX[(11 + 2 * k) * g.stride];
+      Acc128 a;
+      a.lo = lo + plo;
+      a.hi = (long long)(hi + phi + (a.lo < lo ? 1ull : 0ull));
+      const size_t o = ((size_t)k) * nr + r;
+      p.si[(size_t)tc * 10 * nr + o] = __dadd_rn(p.si[(size_t)cidx * 10 * nr + o], a.value(frac));
+      p.sc[(size_t)tc * 10 * nr + o] = p.sc[(size_t)cidx * 10 * nr + o] + g.SX[k * g.stride];
+    }
   }
 
   acc.events += events;
@@ -1488,6 +1548,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
   {
     const int pt_words = ((p.H + 10 * g.hq) * stride + 1) & ~1;   // 8-byte aligned table
     g.PT = reinterpret_cast<unsigned long long*>(smem + pt_words) + (LANES && is_slot ? slot : 0);
+    g.SX = g.PT + 20 * stride;                                       // score mode only
   }
   g.cur_rep = -1;
   g.stride = stride;
@@ -1708,6 +1769,11 @@ __global__ void init_carry_kernel(KParams p, int rep) {
   p.cb[r] = 0.0;
   p.ct[r] = 0.0;
   p.cim[r] = 0.0;
+  if (p.score)
+    for (int k = 0; k < 10; ++k) {
+      p.sc[(size_t)k * p.NR + r] = 0ull;
+      p.si[(size_t)k * p.NR + r] = 0.0;
+    }
   p.cib[r] = 0.0;
   p.rhi[r] = 0ull;    // ring empty
   p.rcidx[r] = 0;
@@ -1787,6 +1853,92 @@ __global__ void gather_carry_kernel(KParams p, int b, unsigned long long* i_out,
   if (t_out) t_out[loc] = p.ct[c];
 }
 
+// ---------------------------------------------------------------- score
+// Per lattice b (one block each): the path statistics summed over its regions
+// (committed copies) in a fixed order -- C_k exactly, I_k by a fixed
+// tree -- then the score dlog L / d(beta, h, J) = sum_k C_k dlog p_k - sum_k dp_k I_k
+// with the lattice's tables tab[b] = {dlog p [3][10], dp [3][10]}.
+// out[b] = {S[3], C[10] (as doubles), I[10]}.
+__global__ void score_kernel(KParams p, const double* tab, double* out) {
+  __shared__ double sd[256];
+  __shared__ unsigned long long su[256];
+  __shared__ double cI[20];
+  const int b = blockIdx.x;
+  const RepDesc& d = p.reps[b];
+  const size_t nr = (size_t)p.NR;
+  for (int k = 0; k < 10; ++k) {
+    double a = 0.0;
+    unsigned long long c = 0ull;
+    for (int loc = threadIdx.x; loc < d.NR; loc += blockDim.x) {
+      const int r = d.off + loc;
+      const size_t o = ((size_t)p.rcidx[r] * 10 + k) * nr + r;
+      a = __dadd_rn(a, p.si[o]);
+      c += p.sc[o];
+    }
+    sd[threadIdx.x] = a;
+    su[threadIdx.x] = c;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) {
+        sd[threadIdx.x] = __dadd_rn(sd[threadIdx.x], sd[threadIdx.x + w]);
+        su[threadIdx.x] += su[threadIdx.x + w];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      cI[k] = (double)su[0];
+      cI[10 + k] = sd[0];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) {
+    const int q = threadIdx.x;
+    const double* dlogp = tab + (size_t)b * 60 + q * 10;
+    const double* dp = tab + (size_t)b * 60 + 30 + q * 10;
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < 10; ++k) {
+      sa = __dadd_rn(sa, __dmul_rn(cI[k], dlogp[k]));
+      sb = __dadd_rn(sb, __dmul_rn(dp[k], cI[10 + k]));
+    }
+    out[(size_t)b * 23 + q] = __dsub_rn(sa, sb);
+  }
+  if (threadIdx.x < 20) out[(size_t)b * 23 + 3 + threadIdx.x] = cI[threadIdx.x];
+}
+
+// Column sums of A [n][m] in a fixed order (one block per column).
+__global__ void colsum_kernel(int n, int m, const double* A, double* sums) {
+  __shared__ double sd[256];
+  const int j = blockIdx.x;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a = __dadd_rn(a, A[(size_t)i * m + j]);
+  sd[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sd[threadIdx.x] = __dadd_rn(sd[threadIdx.x], sd[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[j] = sd[0];
+}
+
+// The backward of time averages A [n][m] through the score: for replica i and
+// parameter q, G[i][q] = sum_j gA[i][j] ((A[i][j] - base_ij) S[i][q] + E[i][j][q]),
+// base_ij the mean of column j over the other replicas (0 when n = 1).
+__global__ void score_grad_kernel(int n, int m, int nq, const double* A, const double* gA,
+                                  const double* S, const double* E, const double* sums, double* G) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nq) return;
+  const int i = t / nq, q = t % nq;
+  double g = 0.0;
+  for (int j = 0; j < m; ++j) {
+    const double a = A[(size_t)i * m + j];
+    const double base = n > 1 ? __ddiv_rn(__dsub_rn(sums[j], a), (double)(n - 1)) : 0.0;
+    double term = __dmul_rn(__dsub_rn(a, base), S[(size_t)i * nq + q]);
+    if (E) term = __dadd_rn(term, E[((size_t)i * m + j) * nq + q]);
+    g = __dadd_rn(g, __dmul_rn(gA[(size_t)i * m + j], term));
+  }
+  G[t] = g;
+}
+
 __global__ void eval_draws_kernel(uint32_t key0, uint32_t key1, uint32_t region,
                                   unsigned long long i0, size_t n, double* x,
                                   unsigned long long* kv) {
@@ -1847,6 +1999,10 @@ struct sr_ctx {
   double* rx;
   int K, Kcap;
   double *cx, *cb, *ct, *cim, *cib, *ht, *trt;
+  unsigned long long* sc;       // score statistics (score mode)
+  double* si;
+  double* score_tab;            // [nrep][2][3][10] dlog p and dp per lattice (score mode)
+  double* score_out;            // [nrep][3 + 20] scores and lattice statistics
   uint8_t* hp;
   int cap;
   bool cap_auto;
@@ -1892,6 +2048,33 @@ void rate_table(const sr_replica& p, int F, unsigned long long P[10]) {
   }
 }
 
+// d log p_k and d p_k with respect to (beta, h, J), beta = 1/T, for the ten
+// classes (Eqs. 2.1-2.3): a class-k flip changes the energy by
+// dE = 2 s (J (2 n_up - 4) + h), so d(beta dE) = (dE, 2 beta s, 2 beta s nb).
+// Metropolis, p = min(1, exp(-beta dE)): d log p = -d(beta dE) where dE > 0,
+// 0 where p = 1.  Glauber, p = e / (1 + e) with e = exp(-beta dE):
+// d log p = -(1 - p) d(beta dE).  tab = {dlog p [3][10], dp [3][10]}.
+void score_tables(const sr_replica& p, double* tab) {
+  const double beta = 1.0 / p.T;
+  for (int k = 0; k < 10; ++k) {
+    const double s = (k >= 5) ? 1.0 : -1.0;
+    const double nb = 2.0 * (double)(k % 5) - 4.0;
+    const double dE = 2.0 * s * (p.J * nb + p.h);
+    const double e = std::exp(-dE / p.T);
+    const double pk = p.rates == SR_RATES_GLAUBER ? e / (1.0 + e) : (e < 1.0 ? e : 1.0);
+    const double dx[3] = {dE, 2.0 * beta * s, 2.0 * beta * s * nb};
+    for (int q = 0; q < 3; ++q) {
+      double dl;
+      if (p.rates == SR_RATES_GLAUBER)
+        dl = -(1.0 - pk) * dx[q];
+      else
+        dl = dE > 0.0 ? -dx[q] : 0.0;
+      tab[q * 10 + k] = dl;
+      tab[30 + q * 10 + k] = pk * dl;
+    }
+  }
+}
+
 KParams make_params(const sr_ctx* c) {
   KParams k;
   std::memset(&k, 0, sizeof k);
@@ -1918,6 +2101,9 @@ KParams make_params(const sr_ctx* c) {
   k.cb = c->cb;
   k.ct = c->ct;
   k.cim = c->cim;
+  k.sc = c->sc;
+  k.si = c->si;
+  k.score = c->prm.score ? 1 : 0;
   k.cib = c->cib;
   k.ht = c->ht;
   k.hp = c->hp;
@@ -1967,10 +2153,11 @@ int alloc_history(sr_ctx* c, int cap) {
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SR_OK : SR_ECUDA; }
 
 // Shared memory of a lane-mapping block: per region slot, H spin rows, ten
-// class counts and ten class-by-row count groups of ceil(H/4) words.
-size_t lane_smem_bytes(int H, int slots) {
+// class-by-row count groups of ceil(H/4) words, the rate table (20 words of
+// 8 bytes) and, in score mode, 30 more 8-byte words of path statistics.
+size_t lane_smem_bytes(int H, int slots, bool score) {
   const size_t words = ((size_t)(H + 10 * ((H + 3) / 4)) * (size_t)slots + 1) & ~(size_t)1;
-  return (words + 40 * (size_t)slots) * sizeof(uint32_t);
+  return (words + (score ? 100 : 40) * (size_t)slots) * sizeof(uint32_t);
 }
 
 // Allow a kernel `bytes` of dynamic shared memory (beyond the default 48 KB,
@@ -2077,7 +2264,8 @@ int set_ring(sr_ctx* c, int K) {
 }
 
 void free_all(sr_ctx* c) {
-  void* dev[] = {c->rows, c->halo, c->hl, c->trs, c->win_iters, c->curf, c->ci, c->ckv, c->cx, c->cb,
+  void* dev[] = {c->sc, c->si, c->score_tab, c->score_out,
+                 c->rows, c->halo, c->hl, c->trs, c->win_iters, c->curf, c->ci, c->ckv, c->cx, c->cb,
                  c->ct, c->cim, c->cib, c->ht, c->trt, c->hp, c->st, c->obs_i, c->obs_f, c->stage,
                  c->rx, c->rkv, c->rhi, c->chg, c->log, c->loghdr, c->desc, c->rs, c->rrep,
                  c->rflags, c->rcidx, c->rfill, c->rn, c->rwin, c->rts};
@@ -2116,6 +2304,8 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     return SR_EINVAL;
   if (p.fresh_steps != 0 && p.fresh_steps != 1) return SR_EINVAL;
   if (p.fresh_steps && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
+  if (p.score != 0 && p.score != 1) return SR_EINVAL;
+  if (p.score && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
   if (p.region_w > 32 || p.region_h > 32) return SR_EUNSUPPORTED;
   for (int b = 0; b < n; ++b) {
     const int rc = check_replica(reps[b], p.region_w, p.region_h);
@@ -2217,7 +2407,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     if (wpb > SR_LANE_MAX_THREADS / 32) wpb = SR_LANE_MAX_THREADS / 32;
     c->rl = wpb * lanes;
     c->tpb = 32 * wpb;
-    c->smem = lane_smem_bytes(H, c->rl);
+    c->smem = lane_smem_bytes(H, c->rl, p.score != 0);
   }
   {
     const void* fn = c->mode == 1 ? (const void*)relax_kernel<1>
@@ -2248,6 +2438,12 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   rc |= dalloc(&c->cb, 2 * nr);
   rc |= dalloc(&c->ct, 2 * nr);
   rc |= dalloc(&c->cim, 2 * nr);
+  if (p.score) {
+    rc |= dalloc(&c->sc, 2 * 10 * nr);
+    rc |= dalloc(&c->si, 2 * 10 * nr);
+    rc |= dalloc(&c->score_tab, (size_t)n * 60);
+    rc |= dalloc(&c->score_out, (size_t)n * 23);
+  }
   rc |= dalloc(&c->cib, 2 * nr);
   rc |= dalloc(&c->hl, 2 * 4 * nr);
   rc |= dalloc(&c->st, 1);
@@ -2268,7 +2464,10 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   rc |= dalloc(&c->rwin, nr);
   rc |= dalloc(&c->rts, nr);
   // incremental replay log: lane mappings only
-  c->CB = (c->mode == 1 || p.replay_records < 0) ? 0 : (p.replay_records ? p.replay_records : 64);
+  // (score mode keeps no checkpoints: a resumed pass would need the statistics
+  // accumulated before its checkpoint)
+  c->CB = (c->mode == 1 || p.replay_records < 0 || p.score) ? 0
+                                                           : (p.replay_records ? p.replay_records : 64);
   if (c->CB > 0) {
     rc |= dalloc(&c->log, nr * (size_t)c->CB * (size_t)(kRecHead + H));
     rc |= dalloc(&c->loghdr, nr * 4);
@@ -2300,6 +2499,18 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   }
   if (rc == SR_OK && cudaMemsetAsync(c->hl, 0, 2 * 4 * nr * sizeof(uint32_t), c->stream) != cudaSuccess)
     rc = SR_ECUDA;
+  if (rc == SR_OK && p.score) {
+    double* tab = (double*)std::malloc((size_t)n * 60 * sizeof(double));
+    if (!tab) {
+      rc = SR_ENOMEM;
+    } else {
+      for (int b = 0; b < n; ++b) score_tables(reps[b], tab + (size_t)b * 60);
+      rc = cuda_rc(cudaMemcpyAsync(c->score_tab, tab, (size_t)n * 60 * sizeof(double),
+                                   cudaMemcpyHostToDevice, c->stream));
+      if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
+      std::free(tab);
+    }
+  }
   if (rc == SR_OK) rc = init_state(c, -1, nullptr);
   if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
   if (rc != SR_OK) {
@@ -2844,6 +3055,58 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
   return SR_OK;
 }
 
+int sr_score(sr_ctx* c, double* out) {
+  if (!c || !out) return SR_EINVAL;
+  if (!c->prm.score) return SR_EUNSUPPORTED;
+  KParams k = make_params(c);
+  score_kernel<<<c->nrep, 256, 0, c->stream>>>(k, c->score_tab, c->score_out);
+  if (cudaGetLastError() != cudaSuccess) return SR_ECUDA;
+  c->launches += 1;
+  double* h = (double*)std::malloc((size_t)c->nrep * 23 * sizeof(double));
+  if (!h) return SR_ENOMEM;
+  int rc = cuda_rc(cudaMemcpyAsync(h, c->score_out, (size_t)c->nrep * 23 * sizeof(double),
+                                   cudaMemcpyDeviceToHost, c->stream));
+  if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
+  if (rc == SR_OK)
+    for (int b = 0; b < c->nrep; ++b)
+      for (int q = 0; q < 3; ++q) out[b * 3 + q] = h[(size_t)b * 23 + q];
+  std::free(h);
+  return rc;
+}
+
+int sr_score_stats(sr_ctx* c, int replica, uint64_t* counts, double* occupancy) {
+  if (!c || replica < 0 || replica >= c->nrep) return SR_EINVAL;
+  if (!c->prm.score) return SR_EUNSUPPORTED;
+  KParams k = make_params(c);
+  score_kernel<<<c->nrep, 256, 0, c->stream>>>(k, c->score_tab, c->score_out);
+  if (cudaGetLastError() != cudaSuccess) return SR_ECUDA;
+  c->launches += 1;
+  double h[23];
+  int rc = cuda_rc(cudaMemcpyAsync(h, c->score_out + (size_t)replica * 23, sizeof h,
+                                   cudaMemcpyDeviceToHost, c->stream));
+  if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
+  if (rc != SR_OK) return rc;
+  for (int q = 0; q < 10; ++q) {
+    if (counts) counts[q] = (uint64_t)h[3 + q];
+    if (occupancy) occupancy[q] = h[13 + q];
+  }
+  return SR_OK;
+}
+
+int sr_score_grad(int n, int m, int nq, const double* A, const double* gA, const double* S,
+                  const double* E, double* G, void* stream) {
+  if (n < 1 || m < 1 || nq < 1 || m > 1024 || !A || !gA || !S || !G) return SR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* sums = nullptr;
+  if (dalloc(&sums, (size_t)m)) return SR_ENOMEM;
+  colsum_kernel<<<m, 256, 0, st>>>(n, m, A, sums);
+  score_grad_kernel<<<(n * nq + 255) / 256, 256, 0, st>>>(n, m, nq, A, gA, S, E, sums, G);
+  int rc = cuda_rc(cudaGetLastError());
+  if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(st));
+  cudaFree(sums);
+  return rc;
+}
+
 int sr_get_info(sr_ctx* c, int* n_regions, int* frac_bits, uint64_t* P, int* threads_per_block,
                 int* blocks) {
   if (!c) return SR_EINVAL;
@@ -3031,7 +3294,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.rl = rl;
   c.lanes = 32;            // lane mapping, every thread of a block a region lane
   c.tpb = tpb;
-  c.smem = lane_smem_bytes(region_h, rl);
+  c.smem = lane_smem_bytes(region_h, rl, false);
   int per_sm_blocks = 0;
   if (!allow_smem((const void*)relax_kernel<0>, c.smem) ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0>, tpb, c.smem) !=
