@@ -54,6 +54,24 @@ HIST_BYTES_PER_BOUNDARY_EVENT = 9 * 2
 HBM_GBS = 6788.3
 
 
+def job_throughput(dist, seconds, committed, device):
+    """Whole-job throughput of independent replicas, one per rank: the units
+    of all ranks over the slowest rank's time.  Returns (max seconds, value)."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(committed)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    t_max = float(t.item())
+    return t_max, float(c.item()) / t_max
+
+
+def replica_seed(rank):
+    """Seed of the lattice simulated by a rank (each rank its own replica)."""
+    return 1 + rank
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -252,7 +270,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    seed = 1 + rank
+    seed = replica_seed(rank)
     stream = torch.cuda.current_stream()
     lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr,
                      lanes_per_warp=args.lpw, time_arith=args.arith)
@@ -309,13 +327,7 @@ def run_ours(args):
         sampler.terminate()
         sampler.wait()
     total_ms = sum(step_ms)
-    t_dev = torch.tensor([total_ms / 1e3], dtype=torch.float64, device="cuda")
-    c_dev = torch.tensor([float(committed_total)], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
-        dist.all_reduce(c_dev, op=dist.ReduceOp.SUM)
-    t_max = float(t_dev.item())
-    value = float(c_dev.item()) / t_max
+    t_max, value = job_throughput(dist, total_ms / 1e3, committed_total, "cuda")
 
     # ---- end to end through the public API with host buffers: upload the
     # initial spins from pinned memory, run, read back observables and spins
@@ -464,6 +476,61 @@ def run_profile_batch(args):
     return 0
 
 
+def run_grad(args):
+    """Gradients of time-averaged m and energy per site with respect to
+    (beta, h, J) by the score function (autograd backward through the
+    library's kernel), against common-random-number central differences
+    (Delta = 1e-3) and, where the chain is in equilibrium, the fluctuation
+    relation dm/dh = beta N Var(m).  Scale "full": 128 replicas of L = 512,
+    t in [50, 200]; "small": 64 replicas of L = 128, t in [10, 40]."""
+    import numpy as np
+    import torch
+
+    import paper_cs_0405053_gb300 as sr
+    from paper_cs_0405053_gb300 import grad
+    torch.cuda.set_device(0)
+    full = args.grad == "full"
+    R, Ls, t1, t2 = (128, 512, 50.0, 200.0) if full else (64, 128, 10.0, 40.0)
+    out = []
+    for T, h in [(1.8, 0.0), (1.8, 0.05), (2.269, 0.0), (2.269, 0.05), (2.8, 0.0), (2.8, 0.05)]:
+        beta = 1.0 / T
+        spec = grad.AverageSpec(L=[Ls] * R, seeds=list(range(7000, 7000 + R)), t1=t1, t2=t2,
+                                init="up" if T < 2.269 else "fair")
+        theta = torch.tensor([[beta, h, 1.0]] * R, dtype=torch.float64, device="cuda",
+                             requires_grad=True)
+        w0 = time.perf_counter()
+        A = grad.time_averages(theta, spec)
+        fwd_s = time.perf_counter() - w0
+        row = {"T": T, "h": h, "init": spec.init, "forward_s": round(fwd_s, 3)}
+        for j, name in enumerate(("m", "e")):
+            theta.grad = None
+            A[:, j].sum().backward(retain_graph=True)
+            g = theta.grad.detach().cpu().numpy()
+            est, se = g.mean(axis=0), g.std(axis=0, ddof=1) / math.sqrt(R)
+            fds, fdse = [], []
+            for q in range(3):
+                tp, tm = theta.detach().clone(), theta.detach().clone()
+                tp[:, q] += 1e-3
+                tm[:, q] -= 1e-3
+                ap = grad._simulate(tp.cpu().numpy(), spec)[0][:, j]
+                am = grad._simulate(tm.cpu().numpy(), spec)[0][:, j]
+                fd = (ap - am) / 2e-3
+                fds.append(float(fd.mean()))
+                fdse.append(float(fd.std(ddof=1) / math.sqrt(R)))
+            row[f"d{name}"] = {
+                "score": [float(v) for v in est], "score_se": [float(v) for v in se],
+                "fd": fds, "fd_se": fdse,
+                "z": [float((est[q] - fds[q]) / math.hypot(se[q], fdse[q])) for q in range(3)]}
+        if T != 2.269:          # equilibrium: the fluctuation relation of the magnetisation
+            _, _, _, ms = grad._simulate(theta.detach().cpu().numpy(), spec, samples=30)
+            row["beta_N_var_m"] = float(beta * Ls * Ls * ms.var(axis=1, ddof=1).mean())
+        out.append(row)
+    print(json.dumps({"grad": args.grad, "replicas": R, "L": Ls, "t": [t1, t2],
+                      "params": "theta = (beta, h, J); d/d theta of the time averages of m and "
+                                "energy per site", "rows": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,7 +552,11 @@ def main():
                     help="checkpoint records per region for incremental replay (0 auto, -1 off)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run only a short slice of the batched workload (for ncu)")
+    ap.add_argument("--grad", choices=["small", "full"], default=None,
+                    help="gradient check of the score-function backward (separate report)")
     args = ap.parse_args()
+    if args.grad:
+        return run_grad(args)
     if args.profile_case:
         return run_profile_case(args)
     if args.profile_batch:

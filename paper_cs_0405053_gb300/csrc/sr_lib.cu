@@ -663,9 +663,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
 #pragma unroll
     for (int n = 0; n < 5; ++n) {
       const uint32_t e = eq_count(s0, s1, s2, n) & g.wmask;
-      const unsigned cu = __popc(e & rw), cd = __popc(e & ~rw);
-      N.add(5 + n, cu);
-      N.add(n, cd);
+      const unsigned cu = __popc(e & rw), cd = __popc(e) - cu;
       cw[5 + n] |= cu << sh;
       cw[n] |= cd << sh;
     }
@@ -673,6 +671,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
 #pragma unroll
       for (int k = 0; k < 10; ++k) {
         g.C[(k * g.hq + (y >> 2)) * g.stride] = cw[k];
+        N.add(k, __vsadu4(cw[k], 0u));     // the four rows' counts of class k
         cw[k] = 0;
       }
     }

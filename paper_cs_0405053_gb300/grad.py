@@ -35,9 +35,10 @@ class AverageSpec:
     settings: dict = field(default_factory=dict)
 
 
-def _simulate(theta: np.ndarray, spec: AverageSpec):
+def _simulate(theta: np.ndarray, spec: AverageSpec, samples: int = 0):
     """Time averages A [R, 2] (m and energy per site over [t1, t2]), scores
-    S [R, 3] and the averages' explicit derivatives E [R, 2, 3]."""
+    S [R, 3] and the averages' explicit derivatives E [R, 2, 3]; with
+    samples > 0 also m at `samples` equally spaced times in (t1, t2]."""
     R = theta.shape[0]
     reps = [dict(L=int(spec.L[i]), J=float(theta[i, 2]), h=float(theta[i, 1]),
                  T=1.0 / float(theta[i, 0]), seed=int(spec.seeds[i]), init=spec.init,
@@ -46,6 +47,12 @@ def _simulate(theta: np.ndarray, spec: AverageSpec):
         if spec.t1 > 0:
             bt.run_adaptive(spec.t1, kappa=spec.kappa)
         o1 = [bt.observables(b) for b in range(R)]
+        msamp = np.zeros((R, max(samples, 0)))
+        for j in range(samples):
+            t = spec.t1 + (spec.t2 - spec.t1) * (j + 1) / samples
+            bt.run_adaptive(t, kappa=spec.kappa)
+            for b in range(R):
+                msamp[b, j] = bt.observables(b).m
         bt.run_adaptive(spec.t2, kappa=spec.kappa)
         o2 = [bt.observables(b) for b in range(R)]
         S = bt.score()
@@ -60,6 +67,8 @@ def _simulate(theta: np.ndarray, spec: AverageSpec):
         A[i, 1] = (-J * dB - h * dM) / n          # energy per site, Eq. 2.1
         E[i, 1, 1] = -dM / n
         E[i, 1, 2] = -dB / n
+    if samples:
+        return A, S, E, msamp
     return A, S, E
 
 
