@@ -91,6 +91,11 @@ typedef struct sr_params {
                                    the integrals of N_k dt (the statistics of the path's score
                                    function, see sr_score); one lane per region, no incremental
                                    replay (SR_EUNSUPPORTED with a warp per region) */
+  int schedule;                 /* regions to slots in each iteration: 1 static (slot s owns
+                                   regions s, s + slots, ...), 2 dynamic (warps claim the next
+                                   regions from a counter; one more grid-wide synchronize per
+                                   iteration), 0 automatic (dynamic for batches or when regions
+                                   outnumber slots) */
   int test_barrier_skip_block;  /* test hook: this block never arrives at a barrier; -1 = off */
   void* stream;                 /* cudaStream_t; NULL = the library creates its own */
 } sr_params;

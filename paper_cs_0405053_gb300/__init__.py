@@ -41,7 +41,7 @@ class _Params(C.Structure):
                 ("lanes_per_region", C.c_int), ("lanes_per_warp", C.c_int), ("time_arith", C.c_int),
                 ("threads_per_block", C.c_int), ("blocks", C.c_int),
                 ("barrier_timeout_ms", C.c_int), ("replay_records", C.c_int),
-                ("fresh_steps", C.c_int), ("score", C.c_int),
+                ("fresh_steps", C.c_int), ("score", C.c_int), ("schedule", C.c_int),
                 ("test_barrier_skip_block", C.c_int),
                 ("stream", C.c_void_p)]
 
@@ -213,7 +213,7 @@ class Lattice:
                  time_arith: int = 0, threads_per_block: int = 0,
                  blocks: int = 0,
                  barrier_timeout_ms: int = 0, replay_records: int = 0,
-                 fresh_steps: bool = False, score: bool = False,
+                 fresh_steps: bool = False, score: bool = False, schedule: int = 0,
                  test_barrier_skip_block: int = -1,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
         lib = library()
@@ -227,7 +227,7 @@ class Lattice:
                       capacity, max_iters, trace_capacity, lanes_per_region, lanes_per_warp,
                       time_arith, threads_per_block, blocks,
                       barrier_timeout_ms, replay_records, int(fresh_steps), int(score),
-                      test_barrier_skip_block, stream)
+                      schedule, test_barrier_skip_block, stream)
         self._ctx = _P()
         _check(lib.sr_create_ex(C.byref(self._ctx), C.byref(prm)), "sr_create_ex")
         n_regions = C.c_int()
@@ -360,10 +360,12 @@ class Lattice:
 
 def _common_params(region, capacity=0, max_iters=0, lanes_per_region=0, lanes_per_warp=0,
                    time_arith=0, threads_per_block=0, blocks=0, barrier_timeout_ms=0,
-                   replay_records=0, stream=None, fresh_steps=False, score=False) -> _Params:
+                   replay_records=0, stream=None, fresh_steps=False, score=False,
+                   schedule=0) -> _Params:
     return _Params(0, 0.0, 0.0, 0.0, region[0], region[1], 0, 0, 0, capacity, max_iters, 0,
                    lanes_per_region, lanes_per_warp, time_arith, threads_per_block, blocks,
-                   barrier_timeout_ms, replay_records, int(fresh_steps), int(score), -1, stream)
+                   barrier_timeout_ms, replay_records, int(fresh_steps), int(score), schedule,
+                   -1, stream)
 
 
 def _replica_array(replicas):
@@ -408,7 +410,7 @@ class Batch:
                  max_iters: int = 0, lanes_per_region: int = 0, lanes_per_warp: int = 0,
                  time_arith: int = 0, threads_per_block: int = 0, blocks: int = 0,
                  barrier_timeout_ms: int = 0, replay_records: int = 0,
-                 fresh_steps: bool = False, score: bool = False,
+                 fresh_steps: bool = False, score: bool = False, schedule: int = 0,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
         lib = library()
         if stream is None and use_torch_stream:
@@ -417,7 +419,7 @@ class Batch:
         self.region = region
         prm = _common_params(region, capacity, max_iters, lanes_per_region, lanes_per_warp,
                              time_arith, threads_per_block, blocks, barrier_timeout_ms,
-                             replay_records, stream, fresh_steps, score)
+                             replay_records, stream, fresh_steps, score, schedule)
         self._arr = arr
         self._ctx = _P()
         _check(lib.sr_create_batch(C.byref(self._ctx), C.cast(arr, C.c_void_p), len(arr),

@@ -36,6 +36,7 @@ enum : unsigned { ST_CAPACITY = 1u, ST_NOT_CONVERGED = 2u, ST_TIMEOUT = 4u };
 // Device-side status and counters.  The first block of fields is cleared by
 // the host before every launch.
 struct DevStats {
+  unsigned work;                // next unclaimed region of the iteration (dynamic schedule)
   unsigned status;
   unsigned bar_count;
   unsigned bar_gen;
@@ -1527,7 +1528,7 @@ __device__ void fill_ring(const KParams& p) {
 // arithmetic; the first `lanes` lanes of every warp are region lanes.  MODE 1:
 // one warp per region.  Region slot j of block b owns regions
 // b*rl + j + k*(gridDim.x*rl).
-template <int MODE>
+template <int MODE, int DYN>
 __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
                                    MODE == 1 ? SR_WARP_MIN_BLOCKS : SR_LANE_MIN_BLOCKS)
     relax_kernel(KParams p) {
@@ -1602,7 +1603,22 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
     ++giter;
     Acc acc = {0u, 0u, 0u, 0u, 0u, 0u, false, false};
     const long long c0 = clock64();
-    for (int r = sfirst; r < p.NR; r += sstride) {
+    // regions of this slot in this iteration: its own (static schedule), or
+    // consecutive regions claimed a warp at a time from a shared counter, so
+    // that slots whose regions are idle take work from busy lattices
+    int r_dyn = -1;
+    auto next_region = [&](int r) -> int {
+      if (!DYN) return r < 0 ? sfirst : r + sstride;
+      const int per_warp = LANES ? p.lanes : 1;
+      unsigned base = 0u;
+      if ((threadIdx.x & 31) == 0) base = atomicAdd(&st->work, (unsigned)per_warp);
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (base >= (unsigned)p.NR) return INT_MAX;
+      const int cand = (int)base + (LANES ? lane : 0);
+      return (is_slot && (!LANES || lane < p.lanes) && cand < p.NR) ? cand : -2;
+    };
+    for (int r = next_region(r_dyn); r != INT_MAX && (DYN || r < p.NR); r = next_region(r)) {
+      if (r < 0 || r >= p.NR) continue;     // dynamic: no region for this lane in this round
       const int b = (int)__ldg(&p.rrep[r]);
       const RepDesc* d = p.reps + b;
       if (p.rwin[r] >= (unsigned)d->nwin) continue;
@@ -1693,6 +1709,12 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
     }
     __syncthreads();
     fill_ring(p);
+    if (DYN) {
+      // another warp may run any region next: its commit and ring top-up
+      // must be complete first
+      if (blockIdx.x == 0 && threadIdx.x == 0) st->work = 0u;
+      if (!grid_barrier(st, p.timeout_cycles)) return;
+    }
   }
 }
 
@@ -2014,6 +2036,7 @@ struct sr_ctx {
   double* h_obs_f;
   int8_t* stage;
   int rl, tpb, blocks, mode, lanes;
+  int dynamic;                  // dynamic region schedule
   size_t smem;
   int last_nwin;
   unsigned long long launches;   // kernels launched by this context
@@ -2151,6 +2174,16 @@ int alloc_history(sr_ctx* c, int cap) {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SR_OK : SR_ECUDA; }
 
+// The kernel instance of a mapping (0 lane/FP64, 1 warp, 2 lane/integer time)
+// and schedule (static or dynamic).
+const void* relax_fn(int mode, bool dynamic) {
+  if (dynamic)
+    return mode == 1 ? (const void*)relax_kernel<1, 1>
+                     : (mode == 2 ? (const void*)relax_kernel<2, 1> : (const void*)relax_kernel<0, 1>);
+  return mode == 1 ? (const void*)relax_kernel<1, 0>
+                   : (mode == 2 ? (const void*)relax_kernel<2, 0> : (const void*)relax_kernel<0, 0>);
+}
+
 // Shared memory of a lane-mapping block: per region slot, H spin rows, ten
 // class-by-row count groups of ceil(H/4) words, the rate table (20 words of
 // 8 bytes) and, in score mode, 30 more 8-byte words of path statistics.
@@ -2217,8 +2250,7 @@ int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
       cudaMemsetAsync(c->curf, 0, 2 * (size_t)c->nrep * sizeof(uint32_t), c->stream) != cudaSuccess)
     return SR_ECUDA;
   void* args[] = {&k};
-  const void* fn = c->mode == 1 ? (const void*)relax_kernel<1>
-                                : (c->mode == 2 ? (const void*)relax_kernel<2> : (const void*)relax_kernel<0>);
+  const void* fn = relax_fn(c->mode, c->dynamic != 0);
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->blocks), dim3(c->tpb), args, c->smem,
                                               c->stream);
   if (e != cudaSuccess) {
@@ -2304,6 +2336,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   if (p.fresh_steps != 0 && p.fresh_steps != 1) return SR_EINVAL;
   if (p.fresh_steps && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
   if (p.score != 0 && p.score != 1) return SR_EINVAL;
+  if (p.schedule < 0 || p.schedule > 2) return SR_EINVAL;
   if (p.score && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
   if (p.region_w > 32 || p.region_h > 32) return SR_EUNSUPPORTED;
   for (int b = 0; b < n; ++b) {
@@ -2409,8 +2442,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     c->smem = lane_smem_bytes(H, c->rl, p.score != 0);
   }
   {
-    const void* fn = c->mode == 1 ? (const void*)relax_kernel<1>
-                                  : (c->mode == 2 ? (const void*)relax_kernel<2> : (const void*)relax_kernel<0>);
+    const void* fn = relax_fn(c->mode, false);
     cudaFuncAttributes fa;
     int per_sm_blocks = 0;
     if (!allow_smem(fn, c->smem) || cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
@@ -2425,6 +2457,23 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     int blocks = p.blocks ? p.blocks : (c->NR + c->rl - 1) / c->rl;
     if (blocks > per_sm_blocks * c->num_sms) blocks = per_sm_blocks * c->num_sms;
     c->blocks = blocks;
+    // dynamic schedule when regions outnumber the slots or several lattices
+    // share the launch
+    c->dynamic = p.schedule == 2 ||
+                 (p.schedule == 0 && (n > 1 || (long long)c->NR > (long long)blocks * c->rl));
+    if (c->dynamic) {
+      // the dynamic instance: same launch bounds; check it fits the same grid
+      const void* fd = relax_fn(c->mode, true);
+      int bd = 0;
+      if (!allow_smem(fd, c->smem) ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, fd, c->tpb, c->smem) != cudaSuccess ||
+          bd * c->num_sms < c->blocks) {
+        cudaGetLastError();
+        free_all(c);
+        std::free(c);
+        return SR_EUNSUPPORTED;
+      }
+    }
   }
 
   int rc = SR_OK;
@@ -3295,8 +3344,8 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.tpb = tpb;
   c.smem = lane_smem_bytes(region_h, rl, false);
   int per_sm_blocks = 0;
-  if (!allow_smem((const void*)relax_kernel<0>, c.smem) ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0>, tpb, c.smem) !=
+  if (!allow_smem((const void*)relax_kernel<0, 0>, c.smem) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0, 0>, tpb, c.smem) !=
           cudaSuccess ||
       per_sm_blocks < 1) {
     cudaGetLastError();
@@ -3325,7 +3374,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
     return SR_ECUDA;
   KParams k = make_params(&c);
   void* args[] = {&k};
-  if (cudaLaunchCooperativeKernel((const void*)relax_kernel<0>, dim3(c.blocks), dim3(c.tpb), args,
+  if (cudaLaunchCooperativeKernel((const void*)relax_kernel<0, 0>, dim3(c.blocks), dim3(c.tpb), args,
                                   c.smem, c.stream) != cudaSuccess) {
     cudaGetLastError();
     return SR_ECUDA;

@@ -58,7 +58,8 @@ NW = [3, 5, 2, 1, 4, 0]
 MAPS = [dict(),
         dict(lanes_per_region=1, lanes_per_warp=3, time_arith=2),
         dict(lanes_per_region=1, lanes_per_warp=32, time_arith=1, replay_records=2),
-        dict(lanes_per_region=32)]
+        dict(lanes_per_region=32),
+        dict(lanes_per_region=1, lanes_per_warp=32, schedule=1)]
 
 
 @pytest.mark.parametrize("m", range(len(MAPS)))
