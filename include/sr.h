@@ -231,7 +231,7 @@ int sr_run_batch_adaptive(sr_ctx* ctx, const double* t_end, const sr_adapt* opts
 /* ---- autotuner ----
  * Chooses, for a batch of lattices, the region shape (among 8x8, 16x16,
  * 32x32, 16x8 and 32x16 that divide every L), the region lanes per warp
- * (automatic, 8, 16, 32) and kappa (4, 8, 16) by timing trial runs of the real
+ * (automatic, 8, 16, 32) and kappa (4, 8, 16, 32) by timing trial runs of the real
  * lattices: each trial creates a context, runs the adaptive runner untimed to
  * t_trial / 2, then timed to t_trial, and scores committed flips per second.
  * One coordinate at a time (shape, then kappa, then lanes per warp).  The

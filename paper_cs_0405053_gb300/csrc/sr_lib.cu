@@ -36,7 +36,8 @@ enum : unsigned { ST_CAPACITY = 1u, ST_NOT_CONVERGED = 2u, ST_TIMEOUT = 4u };
 // Device-side status and counters.  The first block of fields is cleared by
 // the host before every launch.
 struct DevStats {
-  unsigned work;                // next unclaimed region of the iteration (dynamic schedule)
+  unsigned work;                // next unclaimed work-list entry of the iteration (dynamic)
+  unsigned wl_count[2];         // entries of the two work lists (dynamic, by iteration parity)
   unsigned status;
   unsigned bar_count;
   unsigned bar_gen;
@@ -122,6 +123,7 @@ struct KParams {
   uint32_t* curf;               // [2][nrep] f of the running window, by window parity
   int fresh;                    // the alternate step rule of §5
   int score;                    // accumulate the path statistics sc / si
+  uint32_t* wl;                 // [2][NR] regions that need a pass (dynamic schedule)
   int max_iters;
   long long timeout_cycles;
   int skip_block;
@@ -1473,6 +1475,38 @@ __device__ void compute_halo(const KParams& p, const Lat& lt, int r, unsigned ci
   p.halo[3 * nr + r] = hE;
 }
 
+// A region whose inputs for the coming iteration equal those of the last one
+// keeps its tentative state; its lists are carried to the new parity wp.
+__device__ void carry_lists(const KParams& p, int r, int wp, bool spans_x, bool spans_y) {
+  const size_t nr = (size_t)p.NR, cap = (size_t)p.cap;
+  const int rp = wp ^ 1;
+  for (int e = 0; e < 4; ++e) {
+    if ((e < 2 && spans_y) || (e >= 2 && spans_x)) continue;
+    const unsigned n = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
+    for (unsigned j = 0; j < n; ++j) {
+      const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
+      const size_t dst = (((size_t)wp * 4 + e) * cap + j) * nr + r;
+      p.ht[dst] = __ldcg(&p.ht[src]);
+      p.hp[dst] = __ldcg(&p.hp[src]);
+    }
+    p.hl[((size_t)wp * 4 + e) * nr + r] = n;
+  }
+  p.chg[(size_t)wp * nr + r] = 0;
+}
+
+// Append region r to work list `buf` when `want`; the lanes that reach this
+// point together share one atomic.
+__device__ __forceinline__ void wl_append(const KParams& p, unsigned buf, int r, bool want) {
+  const unsigned mask = __activemask();
+  const unsigned bal = __ballot_sync(mask, want);
+  const int leader = __ffs(mask) - 1;
+  const int lane = threadIdx.x & 31;
+  unsigned base = 0u;
+  if (lane == leader && bal) base = atomicAdd(&p.st->wl_count[buf], (unsigned)__popc(bal));
+  base = __shfl_sync(mask, base, leader);
+  if (want) p.wl[(size_t)buf * p.NR + base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)r;
+}
+
 // ---------------------------------------------------------------- persistent kernel
 // The DO(step) / DO(iteration) loops of the §4 procedure for nwin windows.
 // Ring top-up at a window start: the block's threads together draw the pairs of
@@ -1588,10 +1622,15 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
       p.rwin[r] = 0u;
       p.rts[r] = d->t0;
       p.rfill[r] = d->nwin > 0 ? 1 : 0;
+      if (DYN) wl_append(p, 0u, r, d->nwin > 0);     // every region runs iteration 1
     }
   }
   __syncthreads();
   fill_ring(p);
+  if (DYN) {
+    // a region's first pass may run on another block: its state and ring first
+    if (!grid_barrier(st, p.timeout_cycles)) return;
+  }
 
   // ---- the DO(step) / DO(iteration) loops of the §4 procedure, every lattice
   // of the launch in lockstep: one grid-wide synchronize per iteration, after
@@ -1607,15 +1646,21 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
     // consecutive regions claimed a warp at a time from a shared counter, so
     // that slots whose regions are idle take work from busy lattices
     int r_dyn = -1;
+    const unsigned wlb = (giter - 1u) & 1u;          // this iteration's work list
+    const unsigned wln = DYN ? *(volatile unsigned*)&st->wl_count[wlb] : 0u;
     auto next_region = [&](int r) -> int {
-      if (!DYN) return r < 0 ? sfirst : r + sstride;
-      const int per_warp = LANES ? p.lanes : 1;
-      unsigned base = 0u;
-      if ((threadIdx.x & 31) == 0) base = atomicAdd(&st->work, (unsigned)per_warp);
-      base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (base >= (unsigned)p.NR) return INT_MAX;
-      const int cand = (int)base + (LANES ? lane : 0);
-      return (is_slot && (!LANES || lane < p.lanes) && cand < p.NR) ? cand : -2;
+      if constexpr (!DYN) {
+        return r < 0 ? sfirst : r + sstride;
+      } else {
+        const int per_warp = LANES ? p.lanes : 1;
+        unsigned base = 0u;
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(&st->work, (unsigned)per_warp);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= wln) return INT_MAX;
+        const unsigned cand = base + (LANES ? (unsigned)lane : 0u);
+        return (is_slot && (!LANES || lane < p.lanes) && cand < wln)
+                   ? (int)__ldcg(&p.wl[(size_t)wlb * p.NR + cand]) : -2;
+      }
     };
     for (int r = next_region(r_dyn); r != INT_MAX && (DYN || r < p.NR); r = next_region(r)) {
       if (r < 0 || r >= p.NR) continue;     // dynamic: no region for this lane in this round
@@ -1661,13 +1706,18 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
     for (int b = (int)(blockIdx.x * blockDim.x + threadIdx.x); b < p.nrep; b += gridDim.x * blockDim.x)
       p.rflags[((fslot + 2u) % 3u) * p.nrep + b] = 0u;
 
-    // ---- per region: commit or iterate again (statement 3 of §4)
+    // ---- per region: commit or iterate again (statement 3 of §4); with the
+    // dynamic schedule, also the work list of the next iteration: regions
+    // whose inputs did not change are carried over here instead
+    const unsigned wlnext = giter & 1u;
+    if (DYN && blockIdx.x == 0 && threadIdx.x == 0) st->wl_count[wlb] = 0u;   // list after next
     if (is_slot && (LANES || (threadIdx.x & 31) == 0)) {
       for (int r = sfirst; r < p.NR; r += sstride) {
         const int b = (int)__ldg(&p.rrep[r]);
         const RepDesc* d = p.reps + b;
         const unsigned w = p.rwin[r];
-        if (w >= (unsigned)d->nwin) continue;
+        bool want = false;
+        if (w < (unsigned)d->nwin) {
         RepStats* rs = p.rs + b;
         const unsigned n = p.rn[r];
         if (*(volatile unsigned*)&p.rflags[fslot * p.nrep + b] == 0u) {
@@ -1700,11 +1750,33 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
             }
             if (w + 1u == (unsigned)d->nwin) atomicSub(&st->active, 1u);
           }
+          want = w + 1u < (unsigned)d->nwin;      // iteration 1 of its next window
         } else if ((int)n >= p.max_iters) {
           atomicOr(&st->status, ST_NOT_CONVERGED);
         } else {
           p.rn[r] = n + 1u;
+          if (DYN) {
+            // iteration n + 1 reads the neighbours' lists of iteration n
+            const Lat lt = lat_of(p, r);
+            const int rx = lt.loc % lt.NX, ry = lt.loc / lt.NX;
+            const size_t cp = (size_t)(n & 1u) * nr;
+            bool dirty = false;
+            if (!lt.spans_y)
+              dirty = __ldcg(&p.chg[cp + lt.off + ((ry + lt.NY - 1) % lt.NY) * lt.NX + rx]) ||
+                      __ldcg(&p.chg[cp + lt.off + ((ry + 1) % lt.NY) * lt.NX + rx]);
+            if (!lt.spans_x)
+              dirty = dirty || __ldcg(&p.chg[cp + lt.off + ry * lt.NX + (rx + lt.NX - 1) % lt.NX]) ||
+                      __ldcg(&p.chg[cp + lt.off + ry * lt.NX + (rx + 1) % lt.NX]);
+            if (dirty) {
+              want = true;
+            } else {
+              carry_lists(p, r, (int)((n + 1u) & 1u), lt.spans_x, lt.spans_y);
+              atomicAdd(&st->region_skips, 1ull);
+            }
+          }
         }
+        }
+        if (DYN) wl_append(p, wlnext, r, want);
       }
     }
     __syncthreads();
@@ -2011,6 +2083,7 @@ struct sr_ctx {
   RepStats* rs;
   uint32_t *rrep, *rflags;
   uint8_t *rcidx, *rfill;
+  uint32_t* wl;                 // [2][NR] work lists of the dynamic schedule
   uint32_t *rn, *rwin;
   double* rts;
   uint32_t *rows, *halo, *hl, *trs, *win_iters, *log, *loghdr, *curf;
@@ -2113,6 +2186,7 @@ KParams make_params(const sr_ctx* c) {
   k.rwin = c->rwin;
   k.rts = c->rts;
   k.rfill = c->rfill;
+  k.wl = c->wl;
   k.scale = c->scale;
   k.F = c->F;
   k.rows = c->rows;
@@ -2299,7 +2373,7 @@ void free_all(sr_ctx* c) {
                  c->rows, c->halo, c->hl, c->trs, c->win_iters, c->curf, c->ci, c->ckv, c->cx, c->cb,
                  c->ct, c->cim, c->cib, c->ht, c->trt, c->hp, c->st, c->obs_i, c->obs_f, c->stage,
                  c->rx, c->rkv, c->rhi, c->chg, c->log, c->loghdr, c->desc, c->rs, c->rrep,
-                 c->rflags, c->rcidx, c->rfill, c->rn, c->rwin, c->rts};
+                 c->rflags, c->rcidx, c->rfill, c->rn, c->rwin, c->rts, c->wl};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (c->h_st) cudaFreeHost(c->h_st);
@@ -2508,6 +2582,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   rc |= dalloc(&c->rrep, nr);
   rc |= dalloc(&c->rcidx, nr);
   rc |= dalloc(&c->rfill, nr);
+  rc |= dalloc(&c->wl, 2 * nr);
   rc |= dalloc(&c->rn, nr);
   rc |= dalloc(&c->rwin, nr);
   rc |= dalloc(&c->rts, nr);
@@ -3075,8 +3150,8 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
       bh = shapes[s][1];
     }
   }
-  const double kappas[2] = {4.0, 16.0};
-  for (int i = 0; i < 2 && rc == SR_OK; ++i) {
+  const double kappas[3] = {4.0, 16.0, 32.0};
+  for (int i = 0; i < 3 && rc == SR_OK; ++i) {
     double sc = 0.0;
     rc = trial(bw, bh, 0, kappas[i], &sc);
     if (rc == SR_OK && sc > best) {
