@@ -523,7 +523,8 @@ def run_grad(args):
                 "z": [float((est[q] - fds[q]) / math.hypot(se[q], fdse[q])) for q in range(3)]}
         if T != 2.269:          # equilibrium: the fluctuation relation of the magnetisation
             _, _, _, ms = grad._simulate(theta.detach().cpu().numpy(), spec, samples=30)
-            row["beta_N_var_m"] = float(beta * Ls * Ls * ms.var(axis=1, ddof=1).mean())
+            # variance over independent replicas at each sample time, averaged
+            row["beta_N_var_m"] = float(beta * Ls * Ls * ms.var(axis=0, ddof=1).mean())
         out.append(row)
     print(json.dumps({"grad": args.grad, "replicas": R, "L": Ls, "t": [t1, t2],
                       "params": "theta = (beta, h, J); d/d theta of the time averages of m and "

@@ -94,8 +94,11 @@ typedef struct sr_params {
   int schedule;                 /* regions to slots in each iteration: 1 static (slot s owns
                                    regions s, s + slots, ...), 2 dynamic (warps claim the next
                                    regions from a counter; one more grid-wide synchronize per
-                                   iteration), 0 automatic (dynamic for batches or when regions
-                                   outnumber slots) */
+                                   iteration), 3 asynchronous (one lane per region only: each
+                                   lattice iterates and commits on its own through a task queue,
+                                   with no grid-wide synchronize), 0 automatic (asynchronous
+                                   for batches with one lane per region, dynamic for other
+                                   batches or when regions outnumber slots, else static) */
   int test_barrier_skip_block;  /* test hook: this block never arrives at a barrier; -1 = off */
   void* stream;                 /* cudaStream_t; NULL = the library creates its own */
 } sr_params;

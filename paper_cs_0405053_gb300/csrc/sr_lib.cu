@@ -36,6 +36,9 @@ enum : unsigned { ST_CAPACITY = 1u, ST_NOT_CONVERGED = 2u, ST_TIMEOUT = 4u };
 // Device-side status and counters.  The first block of fields is cleared by
 // the host before every launch.
 struct DevStats {
+  unsigned long long qhead, qtail;   // task queue (asynchronous schedule): claimed / published
+  unsigned long long cwork;     // regions with a commit task outstanding (asynchronous); the
+                                // top bit stops new commits after an error
   unsigned work;                // next unclaimed work-list entry of the iteration (dynamic)
   unsigned wl_count[2];         // entries of the two work lists (dynamic, by iteration parity)
   unsigned status;
@@ -71,6 +74,17 @@ struct RepStats {
   unsigned long long sum_f;     // sum over committed windows of f (§6)
   unsigned last_iters, max_iters_seen, max_f, max_win_events;
   unsigned windows_done;        // windows committed in the current launch
+};
+
+// Per-lattice progress of the asynchronous schedule (host-initialised).
+struct LatState {
+  unsigned pend;                // regions of the current task set not finished
+  unsigned chg;                 // a region's lists changed in the current iteration
+  unsigned ovf;                 // a region overflowed its history capacity
+  unsigned n;                   // iteration of the current passes (1-based, per window)
+  unsigned w;                   // windows committed in this launch
+  unsigned pad;
+  double ts;                    // start of the current window
 };
 
 struct KParams {
@@ -124,6 +138,9 @@ struct KParams {
   int fresh;                    // the alternate step rule of §5
   int score;                    // accumulate the path statistics sc / si
   uint32_t* wl;                 // [2][NR] regions that need a pass (dynamic schedule)
+  LatState* ls;                 // [nrep] (asynchronous schedule)
+  unsigned long long* q;        // [qcap] task queue (asynchronous schedule)
+  unsigned long long qcap;
   int max_iters;
   long long timeout_cycles;
   int skip_block;
@@ -652,11 +669,13 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
 
   // ---- class counts N_k (packed in registers, Counts), the per-row class
   // counts in shared memory, Lambda, and the region's spin / owned-bond sums
+  // (recounted from the rows: measured cheaper than storing them with the
+  // state and the checkpoints)
   Counts N;
+  int mag0 = 0, bond0 = 0;
   uint32_t cw[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) cw[k] = 0;
-  int mag0 = 0, bond0 = 0;
   for (int y = 0; y < H; ++y) {
     const uint32_t rw = g.row(y);
     uint32_t up, dn, lf, rt, s0, s1, s2;
@@ -1549,6 +1568,46 @@ __device__ void fill_ring(const KParams& p) {
   __syncthreads();
 }
 
+// Ring top-up of one region by one lane (asynchronous schedule): the pairs of
+// events [max(rhi, i_c), i_c + K) (all K under the alternate step rule, whose
+// window wg starts on new numbers).
+__device__ void fill_own(const KParams& p, int r, const Lat& lt, unsigned wg) {
+  const size_t nr = (size_t)p.NR;
+  const unsigned long long kmask = (unsigned long long)p.K - 1ull;
+  const unsigned long long lo = __ldcg(&p.ci[(size_t)p.rcidx[r] * nr + r]);
+  const unsigned long long hi_old = p.rhi[r];
+  const unsigned long long from = (hi_old > lo && !p.fresh) ? hi_old : lo;
+  const unsigned long long to = lo + (unsigned long long)p.K;
+  for (unsigned long long i = from; i < to; ++i) {
+    double x;
+    unsigned long long kv;
+    if (p.fresh)
+      draw_event_fresh((unsigned)(i - lo), wg, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
+    else
+      draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
+    const size_t a = (size_t)(i & kmask) * nr + r;
+    p.rx[a] = x;
+    p.rkv[a] = kv;
+  }
+  p.rhi[r] = to;
+}
+
+// Task queue of the asynchronous schedule: a task is (kind, lattice, chunk of
+// `chunk` consecutive regions); kinds 0 = pass, 1 = commit.  The publishing
+// thread has made the lattice's state visible first (fence).
+constexpr unsigned long long kTaskValid = 1ull << 62;
+__device__ void enqueue_lattice(const KParams& p, int b, unsigned kind, int chunk) {
+  const int nreg = p.reps[b].NR;
+  const unsigned long long nch = (unsigned long long)((nreg + chunk - 1) / chunk);
+  __threadfence();
+  const unsigned long long base = atomicAdd(&p.st->qtail, nch);
+  for (unsigned long long c = 0; c < nch; ++c) {
+    const unsigned long long item = kTaskValid | ((unsigned long long)kind << 60) |
+                                    ((unsigned long long)b << 32) | c;
+    atomicExch(&p.q[(base + c) % p.qcap], item);
+  }
+}
+
 #ifndef SR_WARP_MIN_BLOCKS
 #define SR_WARP_MIN_BLOCKS 7
 #endif
@@ -1622,7 +1681,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
       p.rwin[r] = 0u;
       p.rts[r] = d->t0;
       p.rfill[r] = d->nwin > 0 ? 1 : 0;
-      if (DYN) wl_append(p, 0u, r, d->nwin > 0);     // every region runs iteration 1
+      if (DYN == 1) wl_append(p, 0u, r, d->nwin > 0);  // every region runs iteration 1
     }
   }
   __syncthreads();
@@ -1630,6 +1689,164 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
   if (DYN) {
     // a region's first pass may run on another block: its state and ring first
     if (!grid_barrier(st, p.timeout_cycles)) return;
+  }
+
+  if constexpr (DYN == 2) {
+    // ---- asynchronous schedule (lane mapping): every lattice advances on its
+    // own.  A warp takes a task (a chunk of one lattice's regions) from the
+    // queue; the warp that finishes the last task of a lattice's iteration
+    // decides for that lattice alone -- iterate again (pass tasks) or commit
+    // (commit tasks, then the next window's pass tasks).  No grid-wide
+    // synchronize; every wait is bounded.
+    if (!LANES) return;
+    constexpr unsigned kStop = ST_CAPACITY | ST_NOT_CONVERGED | ST_TIMEOUT;
+    constexpr unsigned long long kCworkStop = 1ull << 63;
+    // an error stops new work; the commits already published still run, so no
+    // lattice is left half committed (a decision that meets the stop bit
+    // withdraws its commit before publishing it)
+    auto stop_all = [&](unsigned bit) {
+      atomicOr(&st->status, bit);
+      atomicOr(&st->cwork, kCworkStop);
+    };
+    const int CH = p.lanes;
+    for (;;) {
+      unsigned long long item = 0ull;
+      if (lane == 0) {
+        const unsigned long long slot = atomicAdd(&st->qhead, 1ull) % p.qcap;
+        const long long tw0 = clock64();
+        for (;;) {
+          item = *(volatile unsigned long long*)&p.q[slot];
+          if (item) break;
+          if (*(volatile unsigned*)&st->active == 0u) break;           // all lattices done
+          if (*(volatile unsigned*)&st->status & ST_TIMEOUT) break;
+          if (*(volatile unsigned long long*)&st->cwork == kCworkStop) break;  // stopped, drained
+          if (clock64() - tw0 > p.timeout_cycles) {
+            stop_all(ST_TIMEOUT);
+            break;
+          }
+          __nanosleep(128);
+        }
+        if (item) atomicExch(&p.q[slot], 0ull);
+        __threadfence();
+      }
+      item = __shfl_sync(0xFFFFFFFFu, item, 0);
+      if (!item) break;
+      __syncwarp();          // every lane's reads come after lane 0's acquire
+      const unsigned kind = (unsigned)((item >> 60) & 3ull);
+      const int b = (int)((item >> 32) & 0x0FFFFFFFull);
+      const int c = (int)(item & 0xFFFFFFFFull);
+      const RepDesc* d = p.reps + b;
+      LatState* Ls = p.ls + b;
+      const int loc = c * CH + lane;
+      const bool mine = is_slot && lane < CH && loc < d->NR;
+      const int r = d->off + loc;
+      const unsigned cnt = (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, mine));
+      const unsigned w = *(volatile unsigned*)&Ls->w;
+      RepStats* rs = p.rs + b;
+      if (kind == 1u) {
+        // ---- commit of window w (statement 3 of §4): the tentative state of
+        // the converged iteration becomes the committed one
+        if (mine) {
+          const unsigned cnew = p.rcidx[r] ^ 1u;
+          const unsigned long long dc = __ldcg(&p.ci[(size_t)cnew * nr + r]) -
+                                        __ldcg(&p.ci[(size_t)(cnew ^ 1u) * nr + r]);
+          if (dc) atomicAdd(&rs->committed, dc);
+          p.rcidx[r] = (uint8_t)cnew;
+          const Lat lt = lat_of(p, r);
+          compute_halo(p, lt, r, cnew);
+          if (w + 1u < (unsigned)d->nwin) fill_own(p, r, lt, d->w0 + w + 1u);
+        }
+        __syncwarp();        // every lane's writes come before lane 0's release
+        if (lane == 0) {
+          __threadfence();
+          const unsigned old = atomicSub(&Ls->pend, cnt);
+          if (old == cnt) {
+            const unsigned wn = w + 1u;
+            const unsigned n = Ls->n;                 // iterations of window w
+            rs->windows += 1ull;
+            rs->iterations += (unsigned long long)n;
+            rs->last_iters = n;
+            if (n > rs->max_iters_seen) rs->max_iters_seen = n;
+            const unsigned fw = p.curf[(w & 1u) * p.nrep + b];
+            p.curf[(w & 1u) * p.nrep + b] = 0u;
+            rs->sum_f += fw;
+            if (b == 0) {
+              p.win_iters[w % kWinRing] = n;
+              p.win_iters[kWinRing + w % kWinRing] = fw;
+            }
+            Ls->w = wn;
+            rs->windows_done = wn;
+            if (wn < (unsigned)d->nwin && !(*(volatile unsigned*)&st->status & kStop)) {
+              Ls->n = 1u;
+              Ls->chg = 0u;
+              Ls->ovf = 0u;
+              Ls->pend = (unsigned)d->NR;
+              Ls->ts = __dadd_rn(Ls->ts, d->Tw);
+              enqueue_lattice(p, b, 0u, CH);
+            }
+            __threadfence();
+            if (wn == (unsigned)d->nwin) atomicSub(&st->active, 1u);
+          }
+          atomicAdd(&st->cwork, 0ull - (unsigned long long)cnt);
+        }
+      } else {
+        // ---- iteration n of window w; after an error no new passes run
+        if (*(volatile unsigned*)&st->status & kStop) continue;
+        const unsigned n = *(volatile unsigned*)&Ls->n;
+        const double t_s = *(volatile double*)&Ls->ts;
+        const double t_end = __dadd_rn(t_s, d->Tw);
+        Acc ra = {0u, 0u, 0u, 0u, 0u, 0u, false, false};
+        if (mine) {
+          const Lat lt = lat_of(p, r);
+          const unsigned cidx = p.rcidx[r];
+          if (MODE == 2)
+            run_region<1>(p, lt, r, (int)n, cidx, t_s, t_end, d->w0 + w, g, ra);
+          else
+            run_region<0>(p, lt, r, (int)n, cidx, t_s, t_end, d->w0 + w, g, ra);
+          if (ra.fmax) atomicMax(&p.curf[(w & 1u) * p.nrep + b], ra.fmax);
+          if (ra.events) atomicAdd(&rs->generated, (unsigned long long)ra.events);
+          if (ra.breaks) atomicAdd(&rs->breaks, (unsigned long long)ra.breaks);
+          if (ra.fmax) atomicMax(&rs->max_f, ra.fmax);
+          if (ra.emax) atomicMax(&rs->max_win_events, ra.emax);
+          if (ra.passes) atomicAdd(&st->region_passes, (unsigned long long)ra.passes);
+          if (ra.skips) atomicAdd(&st->region_skips, (unsigned long long)ra.skips);
+        }
+        const bool anych = __any_sync(0xFFFFFFFFu, mine && ra.changed);
+        const bool anyov = __any_sync(0xFFFFFFFFu, mine && ra.overflow);
+        __syncwarp();        // every lane's writes come before lane 0's release
+        if (lane == 0) {
+          if (anych) atomicOr(&Ls->chg, 1u);
+          if (anyov) atomicOr(&Ls->ovf, 1u);
+          __threadfence();
+          const unsigned old = atomicSub(&Ls->pend, cnt);
+          if (old == cnt) {
+            __threadfence();
+            const unsigned ch = *(volatile unsigned*)&Ls->chg;
+            const unsigned ov = *(volatile unsigned*)&Ls->ovf;
+            if (ov) {
+              stop_all(ST_CAPACITY);
+            } else if (!ch) {
+              // no region of this lattice changed its lists: the fixed point;
+              // commit tasks follow (the window's statistics count at their end)
+              Ls->pend = (unsigned)d->NR;
+              const unsigned long long before = atomicAdd(&st->cwork, (unsigned long long)d->NR);
+              if (before & kCworkStop)
+                atomicAdd(&st->cwork, 0ull - (unsigned long long)d->NR);   // stopped: no commit
+              else
+                enqueue_lattice(p, b, 1u, CH);
+            } else if ((int)n >= p.max_iters) {
+              stop_all(ST_NOT_CONVERGED);
+            } else if (!(*(volatile unsigned*)&st->status & kStop)) {
+              Ls->n = n + 1u;
+              Ls->chg = 0u;
+              Ls->pend = (unsigned)d->NR;
+              enqueue_lattice(p, b, 0u, CH);
+            }
+          }
+        }
+      }
+    }
+    return;
   }
 
   // ---- the DO(step) / DO(iteration) loops of the §4 procedure, every lattice
@@ -2084,6 +2301,11 @@ struct sr_ctx {
   uint32_t *rrep, *rflags;
   uint8_t *rcidx, *rfill;
   uint32_t* wl;                 // [2][NR] work lists of the dynamic schedule
+  LatState* ls;                 // asynchronous schedule: per-lattice progress
+  unsigned long long* q;        // asynchronous schedule: task queue
+  unsigned long long qcap;
+  unsigned long long async_tail;  // tasks published before the launch (asynchronous schedule)
+  unsigned async_active;
   uint32_t *rn, *rwin;
   double* rts;
   uint32_t *rows, *halo, *hl, *trs, *win_iters, *log, *loghdr, *curf;
@@ -2187,6 +2409,9 @@ KParams make_params(const sr_ctx* c) {
   k.rts = c->rts;
   k.rfill = c->rfill;
   k.wl = c->wl;
+  k.ls = c->ls;
+  k.q = c->q;
+  k.qcap = c->qcap;
   k.scale = c->scale;
   k.F = c->F;
   k.rows = c->rows;
@@ -2250,7 +2475,9 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SR_OK : SR_ECUDA; }
 
 // The kernel instance of a mapping (0 lane/FP64, 1 warp, 2 lane/integer time)
 // and schedule (static or dynamic).
-const void* relax_fn(int mode, bool dynamic) {
+const void* relax_fn(int mode, int dynamic) {
+  if (dynamic == 2)
+    return mode == 2 ? (const void*)relax_kernel<2, 2> : (const void*)relax_kernel<0, 2>;
   if (dynamic)
     return mode == 1 ? (const void*)relax_kernel<1, 1>
                      : (mode == 2 ? (const void*)relax_kernel<2, 1> : (const void*)relax_kernel<0, 1>);
@@ -2319,12 +2546,59 @@ int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
   int rc = upload_desc(c);
   if (rc != SR_OK) return rc;
   KParams k = make_params(c);
+  if (c->dynamic == 2) {
+    // per-lattice progress and the first pass tasks of every lattice with windows
+    LatState* hls = (LatState*)std::calloc((size_t)c->nrep, sizeof(LatState));
+    unsigned long long total = 0ull;
+    unsigned active = 0u;
+    for (int b = 0; b < c->nrep; ++b)
+      if (nwin[b] > 0) {
+        total += (unsigned long long)((c->hdesc[b].NR + c->lanes - 1) / c->lanes);
+        ++active;
+      }
+    unsigned long long* items = (unsigned long long*)std::malloc((size_t)(total + 1) * 8);
+    if (!hls || !items) {
+      std::free(hls);
+      std::free(items);
+      return SR_ENOMEM;
+    }
+    unsigned long long t = 0ull;
+    for (int b = 0; b < c->nrep; ++b) {
+      hls[b].pend = (unsigned)c->hdesc[b].NR;
+      hls[b].n = 1u;
+      hls[b].ts = c->t_c[b];
+      if (nwin[b] <= 0) continue;
+      const int nch = (c->hdesc[b].NR + c->lanes - 1) / c->lanes;
+      for (int ch = 0; ch < nch; ++ch)
+        items[t++] = kTaskValid | ((unsigned long long)b << 32) | (unsigned long long)ch;
+    }
+    int rca = cuda_rc(cudaMemcpyAsync(c->ls, hls, (size_t)c->nrep * sizeof(LatState),
+                                      cudaMemcpyHostToDevice, c->stream));
+    if (rca == SR_OK)
+      rca = cuda_rc(cudaMemsetAsync(c->q, 0, (size_t)c->qcap * 8, c->stream));
+    if (rca == SR_OK && total)
+      rca = cuda_rc(cudaMemcpyAsync(c->q, items, (size_t)total * 8, cudaMemcpyHostToDevice, c->stream));
+    if (rca == SR_OK) rca = cuda_rc(cudaStreamSynchronize(c->stream));
+    std::free(hls);
+    std::free(items);
+    if (rca != SR_OK) return rca;
+    c->async_tail = total;
+    c->async_active = active;
+  }
   if (cudaMemsetAsync(c->st, 0, offsetof(DevStats, region_passes), c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->rflags, 0, 3 * (size_t)c->nrep * sizeof(uint32_t), c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->curf, 0, 2 * (size_t)c->nrep * sizeof(uint32_t), c->stream) != cudaSuccess)
     return SR_ECUDA;
+  if (c->dynamic == 2) {
+    if (cudaMemcpyAsync((char*)c->st + offsetof(DevStats, qtail), &c->async_tail, 8,
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync((char*)c->st + offsetof(DevStats, active), &c->async_active, 4,
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return SR_ECUDA;
+  }
   void* args[] = {&k};
-  const void* fn = relax_fn(c->mode, c->dynamic != 0);
+  const void* fn = relax_fn(c->mode, c->dynamic);
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->blocks), dim3(c->tpb), args, c->smem,
                                               c->stream);
   if (e != cudaSuccess) {
@@ -2373,7 +2647,7 @@ void free_all(sr_ctx* c) {
                  c->rows, c->halo, c->hl, c->trs, c->win_iters, c->curf, c->ci, c->ckv, c->cx, c->cb,
                  c->ct, c->cim, c->cib, c->ht, c->trt, c->hp, c->st, c->obs_i, c->obs_f, c->stage,
                  c->rx, c->rkv, c->rhi, c->chg, c->log, c->loghdr, c->desc, c->rs, c->rrep,
-                 c->rflags, c->rcidx, c->rfill, c->rn, c->rwin, c->rts, c->wl};
+                 c->rflags, c->rcidx, c->rfill, c->rn, c->rwin, c->rts, c->wl, c->ls, c->q};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (c->h_st) cudaFreeHost(c->h_st);
@@ -2410,7 +2684,8 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   if (p.fresh_steps != 0 && p.fresh_steps != 1) return SR_EINVAL;
   if (p.fresh_steps && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
   if (p.score != 0 && p.score != 1) return SR_EINVAL;
-  if (p.schedule < 0 || p.schedule > 2) return SR_EINVAL;
+  if (p.schedule < 0 || p.schedule > 3) return SR_EINVAL;
+  if (p.schedule == 3 && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
   if (p.score && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
   if (p.region_w > 32 || p.region_h > 32) return SR_EUNSUPPORTED;
   for (int b = 0; b < n; ++b) {
@@ -2516,7 +2791,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     c->smem = lane_smem_bytes(H, c->rl, p.score != 0);
   }
   {
-    const void* fn = relax_fn(c->mode, false);
+    const void* fn = relax_fn(c->mode, 0);
     cudaFuncAttributes fa;
     int per_sm_blocks = 0;
     if (!allow_smem(fn, c->smem) || cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
@@ -2533,11 +2808,18 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     c->blocks = blocks;
     // dynamic schedule when regions outnumber the slots or several lattices
     // share the launch
-    c->dynamic = p.schedule == 2 ||
-                 (p.schedule == 0 && (n > 1 || (long long)c->NR > (long long)blocks * c->rl));
+    // automatic: batches in the lane mapping run asynchronously (measured
+    // 19-28% faster than the dynamic lockstep); the warp mapping and single
+    // lattices with more regions than slots use the dynamic lockstep
+    c->dynamic = p.schedule == 3 ? 2
+                 : (p.schedule == 0 && n > 1 && c->mode != 1)
+                       ? 2
+                       : (p.schedule == 2 ||
+                          (p.schedule == 0 && (n > 1 || (long long)c->NR > (long long)blocks * c->rl)))
+                             ? 1 : 0;
     if (c->dynamic) {
       // the dynamic instance: same launch bounds; check it fits the same grid
-      const void* fd = relax_fn(c->mode, true);
+      const void* fd = relax_fn(c->mode, c->dynamic);
       int bd = 0;
       if (!allow_smem(fd, c->smem) ||
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, fd, c->tpb, c->smem) != cudaSuccess ||
@@ -2583,6 +2865,15 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   rc |= dalloc(&c->rcidx, nr);
   rc |= dalloc(&c->rfill, nr);
   rc |= dalloc(&c->wl, 2 * nr);
+  if (c->dynamic == 2) {
+    // at most one task set per lattice is in the queue, plus one claimed slot per warp
+    unsigned long long chunks = 0ull;
+    for (int b = 0; b < n; ++b)
+      chunks += (unsigned long long)((c->hdesc[b].NR + c->lanes - 1) / c->lanes);
+    c->qcap = chunks + (unsigned long long)c->blocks * (unsigned long long)(c->tpb / 32) + 64ull;
+    rc |= dalloc(&c->ls, (size_t)n);
+    rc |= dalloc(&c->q, (size_t)c->qcap);
+  }
   rc |= dalloc(&c->rn, nr);
   rc |= dalloc(&c->rwin, nr);
   rc |= dalloc(&c->rts, nr);

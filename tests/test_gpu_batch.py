@@ -59,7 +59,9 @@ MAPS = [dict(),
         dict(lanes_per_region=1, lanes_per_warp=3, time_arith=2),
         dict(lanes_per_region=1, lanes_per_warp=32, time_arith=1, replay_records=2),
         dict(lanes_per_region=32),
-        dict(lanes_per_region=1, lanes_per_warp=32, schedule=1)]
+        dict(lanes_per_region=1, lanes_per_warp=32, schedule=1),
+        dict(lanes_per_region=1, lanes_per_warp=32, schedule=3),
+        dict(lanes_per_region=1, lanes_per_warp=5, time_arith=2, schedule=3, replay_records=2)]
 
 
 @pytest.mark.parametrize("m", range(len(MAPS)))

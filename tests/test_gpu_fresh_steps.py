@@ -15,7 +15,8 @@ sr = pytest.importorskip("paper_cs_0405053_gb300")
 MAPS = [dict(lanes_per_region=1, lanes_per_warp=32, time_arith=1),
         dict(lanes_per_region=1, lanes_per_warp=3, time_arith=2),
         dict(lanes_per_region=1, lanes_per_warp=2, time_arith=1, replay_records=-1),
-        dict(lanes_per_region=1, lanes_per_warp=5, time_arith=1, replay_records=2)]
+        dict(lanes_per_region=1, lanes_per_warp=5, time_arith=1, replay_records=2),
+        dict(lanes_per_region=1, lanes_per_warp=4, schedule=3)]
 
 
 def _ends(Tw, n, t0=0.0):

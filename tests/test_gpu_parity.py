@@ -102,7 +102,8 @@ MAPS = [dict(lanes_per_region=1, lanes_per_warp=32, time_arith=1),
         dict(lanes_per_region=1, lanes_per_warp=2, time_arith=1, replay_records=-1),
         dict(lanes_per_region=1, lanes_per_warp=5, time_arith=1, replay_records=2),
         dict(lanes_per_region=1, lanes_per_warp=4, schedule=2),
-        dict(lanes_per_region=32, schedule=2)]
+        dict(lanes_per_region=32, schedule=2),
+        dict(lanes_per_region=1, lanes_per_warp=3, schedule=3)]
 LPR = list(range(len(MAPS)))
 
 
