@@ -52,6 +52,22 @@ INT_PEAK_OPS = SMS * LANES_PER_SM * SM_MHZ * 1e6          # 4.03e13 lane-ops/s
 # measured copy bandwidth of this part.
 HIST_BYTES_PER_BOUNDARY_EVENT = 9 * 2
 HBM_GBS = 6788.3
+# DRAM bytes (read + write) of one relaxation launch of each window length,
+# from one ncu capture of the full launch on a GB300:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum #       --clock-control none -k regex:relax_kernel -s 3 -c 1 #       python bench.py --profile-case --tw TW --windows 100/TW
+# valid only for the kernel sources they were taken on (hash below)
+TRAFFIC_BYTES = {0.25: 3209728 + 5869824, 1.0: 26173184 + 75968256, 4.0: 386253568 + 856442880}
+TRAFFIC_SOURCES_SHA = "60bd981714c87ac8"
+
+
+def _kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("paper_cs_0405053_gb300/csrc/sr_lib.cu", "paper_cs_0405053_gb300/csrc/sr_device.cuh",
+              "paper_cs_0405053_gb300/csrc/sr_softfloat.cuh", "include/sr.h"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def job_throughput(dist, seconds, committed, device):
@@ -394,7 +410,11 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "per_window_length": tw_detail},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                     "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "Tops/s", "frac": achieved / peak,
+                     "traffic": (statistics.mean(TRAFFIC_BYTES[t] for t in WINDOWS)
+                                 if _kernel_sources_sha() == TRAFFIC_SOURCES_SHA else None),
+                     "traffic_unit": "bytes per launch (DRAM read + write, mean over the "
+                                     "three window lengths; ncu)",
                      "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz integer issue",
                      "kernel": "relax_kernel", "kernel_ms_avg": kms,
                      "ops_per_committed_event": OPS_PER_EVENT,
@@ -425,7 +445,8 @@ def run_profile_case(args):
     import paper_cs_0405053_gb300 as sr
     torch.cuda.set_device(0)
     lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=1, lanes_per_region=args.lpr,
-                     lanes_per_warp=args.lpw, time_arith=args.arith, replay_records=args.replay)
+                     lanes_per_warp=args.lpw, time_arith=args.arith, replay_records=args.replay,
+                     schedule=args.schedule)
     t0 = None
     for _ in range(args.warmup):
         lat.reset()
@@ -461,7 +482,7 @@ def run_profile_batch(args):
     from paper_cs_0405053_gb300 import workloads
     torch.cuda.set_device(0)
     reps = workloads.batch_replicas()
-    bt = sr.Batch(reps, region=(32, 16), lanes_per_warp=32)
+    bt = sr.Batch(reps, region=(32, 16), lanes_per_warp=32, schedule=args.schedule)
     bt.run_adaptive(1.0, kappa=16.0, chunk=1.0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -546,6 +567,8 @@ def main():
                     help="lanes per region: 1, 32 or 0 (automatic)")
     ap.add_argument("--lpw", type=int, default=0, help="region lanes per warp (lane mapping)")
     ap.add_argument("--arith", type=int, default=0, help="time arithmetic: 1 FP64, 2 integer")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="profile cases: 0 automatic, 1 static, 2 dynamic, 3 asynchronous")
     ap.add_argument("--batch-t", type=float, default=100.0,
                     help="simulated time of the batched section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
