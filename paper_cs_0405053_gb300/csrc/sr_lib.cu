@@ -424,6 +424,19 @@ __device__ __forceinline__ unsigned long long class_pos(unsigned long long D, un
   return j;
 }
 
+// Score mode: an event of class cv and the class moves of its in-region
+// neighbours (class -1: no such neighbour).  Out of line: it keeps the event
+// loop's instruction footprint small when score mode is off (measured 3%).
+__device__ __noinline__ void score_event(const Region& g, int cv, int s_old, int dnb,
+                                        unsigned long long tfix, int cE, int cW, int cS, int cN) {
+  g.SX[cv * g.stride] += 1ull;
+  g.occ_move(cv, cv + (s_old ? -5 : 5), tfix);
+  if (cE >= 0) g.occ_move(cE, cE + dnb, tfix);
+  if (cW >= 0) g.occ_move(cW, cW + dnb, tfix);
+  if (cS >= 0) g.occ_move(cS, cS + dnb, tfix);
+  if (cN >= 0) g.occ_move(cN, cN + dnb, tfix);
+}
+
 // ---------------------------------------------------------------- region pass
 struct Acc {
   unsigned events, breaks, passes, skips;   // per slot and iteration: well below 2^32
@@ -865,14 +878,9 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       const int beta = sig * (nup - 2);
       {
         const unsigned long long tfix = to_fixed(tau, frac);
-        if (p.score) {                 // score statistics of the event and its class moves
-          g.SX[cv * g.stride] += 1ull;
-          g.occ_move(cv, cv + (s_old ? -5 : 5), tfix);
-          if (vE) g.occ_move(cE, cE + dnb, tfix);
-          if (vW) g.occ_move(cW, cW + dnb, tfix);
-          if (vS) g.occ_move(cS, cS + dnb, tfix);
-          if (vN) g.occ_move(cN, cN + dnb, tfix);
-        }
+        if (p.score)                   // score statistics of the event and its class moves
+          score_event(g, cv, s_old, dnb, tfix, vE ? cE : -1, vW ? cW : -1, vS ? cS : -1,
+                      vN ? cN : -1);
         ksig += sig;
         ssig.add(sig, tfix);
         kbeta += beta;
