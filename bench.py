@@ -56,8 +56,8 @@ HBM_GBS = 6788.3
 # from one ncu capture of the full launch on a GB300:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum #       --clock-control none -k regex:relax_kernel -s 3 -c 1 #       python bench.py --profile-case --tw TW --windows 100/TW
 # valid only for the kernel sources they were taken on (hash below)
-TRAFFIC_BYTES = {0.25: 3209728 + 5869824, 1.0: 26173184 + 75968256, 4.0: 386253568 + 856442880}
-TRAFFIC_SOURCES_SHA = "60bd981714c87ac8"
+TRAFFIC_BYTES = {0.25: 3278592 + 5105152, 1.0: 26347776 + 77268224, 4.0: 408691712 + 849872640}
+TRAFFIC_SOURCES_SHA = "e12b0ca9a23c21a7"
 
 
 def _kernel_sources_sha():
