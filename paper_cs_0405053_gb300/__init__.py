@@ -411,6 +411,7 @@ class Batch:
                  time_arith: int = 0, threads_per_block: int = 0, blocks: int = 0,
                  barrier_timeout_ms: int = 0, replay_records: int = 0,
                  fresh_steps: bool = False, score: bool = False, schedule: int = 0,
+                 test_barrier_skip_block: int = -1,
                  stream: Optional[int] = None, use_torch_stream: bool = True):
         lib = library()
         if stream is None and use_torch_stream:
@@ -420,6 +421,7 @@ class Batch:
         prm = _common_params(region, capacity, max_iters, lanes_per_region, lanes_per_warp,
                              time_arith, threads_per_block, blocks, barrier_timeout_ms,
                              replay_records, stream, fresh_steps, score, schedule)
+        prm.test_barrier_skip_block = test_barrier_skip_block
         self._arr = arr
         self._ctx = _P()
         _check(lib.sr_create_batch(C.byref(self._ctx), C.cast(arr, C.c_void_p), len(arr),

@@ -218,3 +218,55 @@ def test_batched_workload_sample_bit_exact():
         assert np.all(batch.t_c == 0.25)
         for b in range(0, len(reps), 11):
             _check_at(batch, b, 16, 16, 0.25)
+
+
+# ----------------------------------------------------------------- errors in a batch
+def _consistent_with_oracle(batch, W, H):
+    """Every lattice's committed state equals the oracle at its own t_c."""
+    for b, r in enumerate(batch.replicas):
+        t = float(batch.t_c[b])
+        ref = oracle.run(r.L, r.J, r.h, r.T, W, H, r.seed, [t], init_mode=INIT[r.init],
+                         glauber=(r.rates == "glauber"))
+        assert np.array_equal(batch.spins(b), ref.spins[-1]), (b, t)
+        i, x, bb, tl = batch.carry(b)
+        if t > 0:
+            assert np.array_equal(i, ref.carry_i), (b, t)
+
+
+@pytest.mark.parametrize("schedule", [2, 3])
+def test_batch_capacity_overflow_keeps_every_lattice_consistent(schedule):
+    reps = [dict(L=16, T=1.0, h=0.1, seed=41), dict(L=64, T=3.5, h=0.0, seed=42),
+            dict(L=8, T=2.0, h=0.0, seed=43)]
+    with sr.Batch(reps, region=(8, 8), capacity=2, schedule=schedule) as bt:
+        with pytest.raises(sr.SRError) as e:
+            bt.run([0.5, 2.0, 0.5], [4, 3, 4])
+        assert e.value.code == sr.SR_CAPACITY
+        assert bt.t_c[1] == 0.0            # the hot lattice never committed a window
+        _consistent_with_oracle(bt, 8, 8)
+
+
+@pytest.mark.parametrize("schedule", [2, 3])
+def test_batch_iteration_cap_keeps_every_lattice_consistent(schedule):
+    # the single-region lattice converges in one iteration, the others cannot
+    reps = [dict(L=8, T=2.0, h=0.1, seed=51), dict(L=32, T=2.5, h=0.05, seed=52)]
+    with sr.Batch(reps, region=(8, 8), max_iters=1, schedule=schedule) as bt:
+        with pytest.raises(sr.SRError) as e:
+            bt.run(1.0, 3)
+        assert e.value.code == sr.SR_NOT_CONVERGED
+        assert bt.t_c[1] == 0.0
+        _consistent_with_oracle(bt, 8, 8)
+
+
+@pytest.mark.parametrize("schedule", [2, 3])
+def test_batch_wait_times_out_instead_of_hanging(schedule):
+    reps = [dict(L=32, T=2.0, h=0.0, seed=61), dict(L=16, T=1.5, h=0.1, seed=62)]
+    with sr.Batch(reps, region=(8, 8), schedule=schedule, threads_per_block=32,
+                  barrier_timeout_ms=100, test_barrier_skip_block=0) as bt:
+        assert bt.blocks >= 2
+        with pytest.raises(sr.SRError) as e:
+            bt.run(1.0, 2)
+        assert e.value.code == sr.SR_TIMEOUT
+    # the GPU context is still usable
+    with sr.Batch(reps, region=(8, 8), schedule=schedule) as bt:
+        bt.run(1.0, 2)
+        _consistent_with_oracle(bt, 8, 8)
