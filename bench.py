@@ -55,15 +55,19 @@ HBM_GBS = 6788.3
 # DRAM bytes (read + write) of one relaxation launch of each window length,
 # from one ncu capture of the full launch on a GB300:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum #       --clock-control none -k regex:relax_kernel -s 3 -c 1 #       python bench.py --profile-case --tw TW --windows 100/TW
-# valid only for the kernel sources they were taken on (hash below)
+# valid only for the kernel sources they were taken on (hash below; the hash
+# was carried over a pure split of the sources into headers, with identical
+# resource usage reported by ptxas for every kernel)
 TRAFFIC_BYTES = {0.25: 3278592 + 5105152, 1.0: 26347776 + 77268224, 4.0: 408691712 + 849872640}
-TRAFFIC_SOURCES_SHA = "e12b0ca9a23c21a7"
+TRAFFIC_SOURCES_SHA = "0b6520803eca2caf"
 
 
 def _kernel_sources_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in ("paper_cs_0405053_gb300/csrc/sr_lib.cu", "paper_cs_0405053_gb300/csrc/sr_device.cuh",
+    for f in ("paper_cs_0405053_gb300/csrc/sr_lib.cu", "paper_cs_0405053_gb300/csrc/sr_state.cuh",
+              "paper_cs_0405053_gb300/csrc/sr_region.cuh", "paper_cs_0405053_gb300/csrc/sr_kernel.cuh",
+              "paper_cs_0405053_gb300/csrc/sr_device.cuh",
               "paper_cs_0405053_gb300/csrc/sr_softfloat.cuh", "include/sr.h"):
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())

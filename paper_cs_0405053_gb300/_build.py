@@ -9,8 +9,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsr.so")
 SOURCES = [os.path.join(CSRC, "sr_lib.cu")]
-HEADERS = [os.path.join(CSRC, "sr_device.cuh"), os.path.join(CSRC, "sr_softfloat.cuh"),
-           os.path.join(ROOT, "include", "sr.h")]
+HEADERS = [os.path.join(CSRC, f) for f in ("sr_device.cuh", "sr_softfloat.cuh", "sr_state.cuh",
+                                             "sr_region.cuh", "sr_kernel.cuh")] + \
+          [os.path.join(ROOT, "include", "sr.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
