@@ -54,12 +54,12 @@ HIST_BYTES_PER_BOUNDARY_EVENT = 9 * 2
 HBM_GBS = 6788.3
 # DRAM bytes (read + write) of one relaxation launch of each window length,
 # from one ncu capture of the full launch on a GB300:
-#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum #       --clock-control none -k regex:relax_kernel -s 3 -c 1 #       python bench.py --profile-case --tw TW --windows 100/TW
-# valid only for the kernel sources they were taken on (hash below; the hash
-# was carried over a pure split of the sources into headers, with identical
-# resource usage reported by ptxas for every kernel)
-TRAFFIC_BYTES = {0.25: 3278592 + 5105152, 1.0: 26347776 + 77268224, 4.0: 408691712 + 849872640}
-TRAFFIC_SOURCES_SHA = "0b6520803eca2caf"
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
+#       --clock-control none -k regex:relax_kernel -s 3 -c 1 \
+#       python bench.py --profile-case --tw TW --windows 100/TW
+# valid only for the kernel sources they were taken on (hash below)
+TRAFFIC_BYTES = {0.25: 3221504 + 4867840, 1.0: 26253056 + 76587008, 4.0: 405394688 + 842491904}
+TRAFFIC_SOURCES_SHA = "32f0950855101d66"
 
 
 def _kernel_sources_sha():

@@ -193,13 +193,22 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
       unsigned long long item = 0ull;
       if (lane == 0) {
         const unsigned long long slot = atomicAdd(&st->qhead, 1ull) % p.qcap;
-        const long long tw0 = clock64();
+        // the wait ends with SR_TIMEOUT only after a whole timeout in which no
+        // task was published anywhere: when one small lattice is left, the
+        // waiting warps are served a few per iteration, in the order they came
+        long long tw0 = clock64();
+        unsigned long long seen = *(volatile unsigned long long*)&st->qtail;
         for (;;) {
           item = *(volatile unsigned long long*)&p.q[slot];
           if (item) break;
           if (*(volatile unsigned*)&st->active == 0u) break;           // all lattices done
           if (*(volatile unsigned*)&st->status & ST_TIMEOUT) break;
           if (*(volatile unsigned long long*)&st->cwork == kCworkStop) break;  // stopped, drained
+          const unsigned long long qt = *(volatile unsigned long long*)&st->qtail;
+          if (qt != seen) {
+            seen = qt;
+            tw0 = clock64();
+          }
           if (clock64() - tw0 > p.timeout_cycles) {
             stop_all(ST_TIMEOUT);
             break;
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
             if (dirty) {
               want = true;
             } else {
-              carry_lists(p, r, (int)((n + 1u) & 1u), lt.spans_x, lt.spans_y);
+              carry_lists(p, r, n + 1u, lt.spans_x, lt.spans_y);
               atomicAdd(&st->region_skips, 1ull);
             }
           }

@@ -55,11 +55,15 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   // ---- a region whose neighbours' lists did not change in the last iteration
   // sees the same input as then, so its output is the same: keep the
   // tentative state and carry the lists over instead of replaying the window
+  // (when the last iteration left the lists as the one before it did, both in
+  // this window, the buffer of parity wp already holds them)
   auto carry_over = [&]() {
+    const bool copy = n_iter < 3 || __ldcg(&p.chg[(size_t)rp * nr + r]) != 0;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      if (!has[e]) continue;
+      if (!has[e] || !copy) continue;
       const unsigned n = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
+#pragma unroll 4
       for (unsigned j = 0; j < n; ++j) {
         const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
         const size_t dst = (((size_t)wp * 4 + e) * cap + j) * nr + r;
@@ -1070,14 +1074,19 @@ __device__ void compute_halo(const KParams& p, const Lat& lt, int r, unsigned ci
   p.halo[3 * nr + r] = hE;
 }
 
-// A region whose inputs for the coming iteration equal those of the last one
-// keeps its tentative state; its lists are carried to the new parity wp.
-__device__ void carry_lists(const KParams& p, int r, int wp, bool spans_x, bool spans_y) {
+// A region whose inputs for iteration n_new equal those of the last one keeps
+// its tentative state; its lists are carried to the new parity.  When the last
+// iteration left them as the one before it did (both in this window), the
+// buffer of the new parity already holds them.
+__device__ void carry_lists(const KParams& p, int r, unsigned n_new, bool spans_x, bool spans_y) {
   const size_t nr = (size_t)p.NR, cap = (size_t)p.cap;
+  const int wp = (int)(n_new & 1u);
   const int rp = wp ^ 1;
+  const bool copy = n_new < 3u || __ldcg(&p.chg[(size_t)rp * nr + r]) != 0;
   for (int e = 0; e < 4; ++e) {
-    if ((e < 2 && spans_y) || (e >= 2 && spans_x)) continue;
+    if ((e < 2 && spans_y) || (e >= 2 && spans_x) || !copy) continue;
     const unsigned n = __ldcg(&p.hl[((size_t)rp * 4 + e) * nr + r]);
+#pragma unroll 4
     for (unsigned j = 0; j < n; ++j) {
       const size_t src = (((size_t)rp * 4 + e) * cap + j) * nr + r;
       const size_t dst = (((size_t)wp * 4 + e) * cap + j) * nr + r;

@@ -257,6 +257,18 @@ def test_batch_iteration_cap_keeps_every_lattice_consistent(schedule):
         _consistent_with_oracle(bt, 8, 8)
 
 
+def test_async_waits_outlast_a_long_tail():
+    """When one small hot lattice is left, each of its iterations publishes one
+    task and the waiting warps (here about 1200) are served one per iteration;
+    their waits, bounded at 25 ms, must count time without any progress only."""
+    reps = [dict(L=64, T=3.5, h=0.0, seed=71), dict(L=32, T=1.0, h=0.1, seed=72)]
+    with sr.Batch(reps, region=(32, 32), schedule=3, blocks=300, threads_per_block=128,
+                  barrier_timeout_ms=25) as bt:
+        bt.run([1.0, 1.0], [3, 1])
+        assert bt.t_c[0] == 3.0 and bt.t_c[1] == 1.0
+        _consistent_with_oracle(bt, 32, 32)
+
+
 @pytest.mark.parametrize("schedule", [2, 3])
 def test_batch_wait_times_out_instead_of_hanging(schedule):
     reps = [dict(L=32, T=2.0, h=0.0, seed=61), dict(L=16, T=1.5, h=0.1, seed=62)]
