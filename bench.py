@@ -58,8 +58,8 @@ HBM_GBS = 6788.3
 #       --clock-control none -k regex:relax_kernel -s 3 -c 1 \
 #       python bench.py --profile-case --tw TW --windows 100/TW
 # valid only for the kernel sources they were taken on (hash below)
-TRAFFIC_BYTES = {0.25: 3221504 + 4867840, 1.0: 26253056 + 76587008, 4.0: 405394688 + 842491904}
-TRAFFIC_SOURCES_SHA = "32f0950855101d66"
+TRAFFIC_BYTES = {0.25: 3482112 + 4785152, 1.0: 27091456 + 77085440, 4.0: 408394496 + 842041600}
+TRAFFIC_SOURCES_SHA = "ef924ef1d1aaaa93"
 
 
 def _kernel_sources_sha():

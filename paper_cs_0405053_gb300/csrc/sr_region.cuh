@@ -478,14 +478,16 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
             const size_t a = (((size_t)wp * 4 + e) * cap + n) * nr + r;
             p.ht[a] = tau;
             p.hp[a] = (uint8_t)pos;
-            if (n < plen(e)) {
-              const size_t pa = (((size_t)rp * 4 + e) * cap + n) * nr + r;
-              if (__double_as_longlong(__ldcg(&p.ht[pa])) != __double_as_longlong(tau) ||
-                  __ldcg(&p.hp[pa]) != (uint8_t)pos)
-                changed = true;
-            } else {
-              changed = true;
-            }
+            // the comparison with the last iteration's list (§4, statement
+            // (c)) takes no branch on its loads, so the event chain does not
+            // wait for them; only the pass end reads the flag (an entry past
+            // the old length is read but does not count)
+            const size_t pa = (((size_t)rp * 4 + e) * cap + n) * nr + r;
+            const unsigned differs =
+                (unsigned)(n >= plen(e)) |
+                (unsigned)(__double_as_longlong(__ldcg(&p.ht[pa])) != __double_as_longlong(tau)) |
+                (unsigned)(__ldcg(&p.hp[pa]) != (uint8_t)pos);
+            changed = changed | (differs != 0u);
             olen[e] = n + 1;
           }
         }
