@@ -298,6 +298,30 @@ int sr_get_spins_replica(sr_ctx* ctx, int replica, int8_t* host_out, size_t n);
 int sr_get_carry_replica(sr_ctx* ctx, int replica, uint64_t* index, double* x, double* b,
                          double* t_last, size_t n);
 
+/* Checkpoint and resume (§5, "Subsequent steps": the state a window carries
+ * to the next is the committed spins, the pending event's index and random
+ * pair, the hazard b accrued since t_last, and t_last).  A checkpoint holds,
+ * for every lattice of ctx, its committed time, committed windows and
+ * counters (sr_obs), and per region the committed spin rows, that clock
+ * carry, the running integrals of the spin sum and of the owned bonds and, in
+ * score mode, the path statistics.  Ring contents and boundary histories are
+ * not kept: the presimulated pairs are a function of the event index, and
+ * every window starts from empty histories (§5, "Statement 2").  A context
+ * loaded from a checkpoint continues bit for bit as the saved one would.
+ * The format is this build's own (native byte order, checked by a tag).
+ *   sr_checkpoint_size: *bytes = the size of ctx's checkpoint.
+ *   sr_checkpoint_save: write it to `buf`, caller-owned host memory of `bytes`.
+ *   sr_checkpoint_load: restore it into ctx, whose lattices must have the same
+ *     L, J, h, T, seed and rates, and the same region shape, score mode and
+ *     step rule, as the saved context's; the trace (sr_get_trace) is not
+ *     restored.
+ * Errors: SR_EINVAL (null pointers, a size other than the checkpoint's, or a
+ * checkpoint that does not match ctx; ctx is then unchanged), SR_ENOMEM,
+ * SR_ECUDA. */
+int sr_checkpoint_size(sr_ctx* ctx, size_t* bytes);
+int sr_checkpoint_save(sr_ctx* ctx, void* buf, size_t bytes);
+int sr_checkpoint_load(sr_ctx* ctx, const void* buf, size_t bytes);
+
 /* Free everything; NULL-safe. */
 void sr_destroy(sr_ctx* ctx);
 

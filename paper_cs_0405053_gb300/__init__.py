@@ -158,6 +158,9 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_score_grad": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]),
             "sr_autotune": (C.c_int, [_P, C.c_int, C.POINTER(_Params), C.c_double,
                                       C.POINTER(_Tune)]),
+            "sr_checkpoint_size": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+            "sr_checkpoint_save": (C.c_int, [_P, _P, C.c_size_t]),
+            "sr_checkpoint_load": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -165,6 +168,20 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def _checkpoint(ctx) -> bytes:
+    lib = library()
+    n = C.c_size_t()
+    _check(lib.sr_checkpoint_size(ctx, C.byref(n)), "sr_checkpoint_size")
+    buf = C.create_string_buffer(n.value)
+    _check(lib.sr_checkpoint_save(ctx, buf, n.value), "sr_checkpoint_save")
+    return buf.raw
+
+
+def _load_checkpoint(ctx, data: bytes) -> None:
+    data = bytes(data)
+    _check(library().sr_checkpoint_load(ctx, data, len(data)), "sr_checkpoint_load")
 
 
 def _check(code: int, what: str) -> None:
@@ -306,6 +323,15 @@ class Lattice:
     def reset(self) -> None:
         _check(library().sr_reset(self._ctx), "sr_reset")
         self.t_c = 0.0
+
+    def checkpoint(self) -> bytes:
+        """The committed state (spins, clock carry, integrals, counters) as
+        bytes; load_checkpoint on a context of the same lattice resumes it."""
+        return _checkpoint(self._ctx)
+
+    def load_checkpoint(self, data: bytes) -> None:
+        _load_checkpoint(self._ctx, data)
+        self.t_c = self.observables().t_c
 
     def carry(self):
         n = self.n_regions
@@ -482,6 +508,15 @@ class Batch:
     def reset(self) -> None:
         _check(library().sr_reset(self._ctx), "sr_reset")
         self.t_c[:] = 0.0
+
+    def checkpoint(self) -> bytes:
+        """The committed state of every lattice as bytes (see Lattice.checkpoint)."""
+        return _checkpoint(self._ctx)
+
+    def load_checkpoint(self, data: bytes) -> None:
+        _load_checkpoint(self._ctx, data)
+        for b in range(len(self.replicas)):
+            self.t_c[b] = self.observables(b).t_c
 
     def observables(self, b: int) -> Observables:
         o = _Obs()

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "sr.h"
 #include "sr_kernel.cuh"
@@ -826,6 +827,173 @@ int carry_of(sr_ctx* c, int b, uint64_t* index, double* x, double* bb, double* t
   return rc;
 }
 
+// ---------------------------------------------------------------- checkpoints
+// A checkpoint in host memory: a header, one record per lattice, then each
+// state array as [m][NR] (the committed copy of every region), in the order
+// rows, ci, cx, ckv, cb, ct, cim, cib and, in score mode, sc, si.
+constexpr uint64_t kCkptTag = 0x31305450434b5253ull;   // "SRKCPT01" read as bytes
+struct CkptHeader {
+  uint64_t tag;
+  int32_t nrep, NR, W, H, score, fresh;
+};
+struct CkptRep {
+  int32_t L, rates;
+  uint64_t seed;
+  double J, h, T, t_c;
+  uint32_t wins, pad;
+  RepStats rs;
+};
+
+size_t ckpt_bytes(const sr_ctx* c) {
+  const size_t nr = (size_t)c->NR, H = (size_t)c->prm.region_h;
+  size_t b = sizeof(CkptHeader) + (size_t)c->nrep * sizeof(CkptRep);
+  b += H * nr * sizeof(uint32_t);                     // spin rows
+  b += 7 * nr * 8;                                    // ci, cx, ckv, cb, ct, cim, cib
+  if (c->prm.score) b += 20 * nr * 8;                 // sc, si
+  return b;
+}
+
+// Append the committed copy of a [2][m][NR] device array to `out`.
+template <class T>
+int ckpt_pull(sr_ctx* c, const T* dev, size_t m, const std::vector<uint8_t>& cidx,
+              unsigned char*& out) {
+  const size_t nr = (size_t)c->NR;
+  std::vector<T> h(2 * m * nr);
+  if (cudaMemcpyAsync(h.data(), dev, h.size() * sizeof(T), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  for (size_t j = 0; j < m; ++j)
+    for (size_t r = 0; r < nr; ++r) {
+      std::memcpy(out, &h[((size_t)cidx[r] * m + j) * nr + r], sizeof(T));
+      out += sizeof(T);
+    }
+  return SR_OK;
+}
+
+// Copy the next [m][NR] block of `in` to copy 0 of a [2][m][NR] device array.
+template <class T>
+int ckpt_push(sr_ctx* c, T* dev, size_t m, const unsigned char*& in) {
+  const size_t n = m * (size_t)c->NR;
+  std::vector<T> h(n);
+  std::memcpy(h.data(), in, n * sizeof(T));
+  in += n * sizeof(T);
+  if (cudaMemcpyAsync(dev, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  return SR_OK;
+}
+
+int ckpt_save(sr_ctx* c, unsigned char* out) {
+  const size_t nr = (size_t)c->NR, H = (size_t)c->prm.region_h;
+  std::vector<uint8_t> cidx(nr);
+  std::vector<RepStats> rs((size_t)c->nrep);
+  if (cudaMemcpyAsync(cidx.data(), c->rcidx, nr, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(rs.data(), c->rs, rs.size() * sizeof(RepStats), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof hd);
+  hd.tag = kCkptTag;
+  hd.nrep = c->nrep;
+  hd.NR = c->NR;
+  hd.W = c->prm.region_w;
+  hd.H = c->prm.region_h;
+  hd.score = c->prm.score ? 1 : 0;
+  hd.fresh = c->prm.fresh_steps ? 1 : 0;
+  std::memcpy(out, &hd, sizeof hd);
+  out += sizeof hd;
+  for (int b = 0; b < c->nrep; ++b) {
+    CkptRep cr;
+    std::memset(&cr, 0, sizeof cr);
+    cr.L = c->reps[b].L;
+    cr.rates = c->reps[b].rates;
+    cr.seed = c->reps[b].seed;
+    cr.J = c->reps[b].J;
+    cr.h = c->reps[b].h;
+    cr.T = c->reps[b].T;
+    cr.t_c = c->t_c[b];
+    cr.wins = c->wins[b];
+    cr.rs = rs[(size_t)b];
+    std::memcpy(out, &cr, sizeof cr);
+    out += sizeof cr;
+  }
+  int rc = ckpt_pull(c, c->rows, H, cidx, out);
+  if (rc == SR_OK) rc = ckpt_pull(c, c->ci, 1, cidx, out);
+  if (rc == SR_OK) rc = ckpt_pull(c, c->cx, 1, cidx, out);
+  if (rc == SR_OK) rc = ckpt_pull(c, c->ckv, 1, cidx, out);
+  if (rc == SR_OK) rc = ckpt_pull(c, c->cb, 1, cidx, out);
+  if (rc == SR_OK) rc = ckpt_pull(c, c->ct, 1, cidx, out);
+  if (rc == SR_OK) rc = ckpt_pull(c, c->cim, 1, cidx, out);
+  if (rc == SR_OK) rc = ckpt_pull(c, c->cib, 1, cidx, out);
+  if (rc == SR_OK && c->prm.score) rc = ckpt_pull(c, c->sc, 10, cidx, out);
+  if (rc == SR_OK && c->prm.score) rc = ckpt_pull(c, c->si, 10, cidx, out);
+  return rc;
+}
+
+// The checkpoint at `in` fits context c: same lattices, region shape and modes.
+bool ckpt_matches(const sr_ctx* c, const unsigned char* in) {
+  CkptHeader hd;
+  std::memcpy(&hd, in, sizeof hd);
+  if (hd.tag != kCkptTag || hd.nrep != c->nrep || hd.NR != c->NR || hd.W != c->prm.region_w ||
+      hd.H != c->prm.region_h || hd.score != (c->prm.score ? 1 : 0) ||
+      hd.fresh != (c->prm.fresh_steps ? 1 : 0))
+    return false;
+  in += sizeof hd;
+  for (int b = 0; b < c->nrep; ++b) {
+    CkptRep cr;
+    std::memcpy(&cr, in + (size_t)b * sizeof cr, sizeof cr);
+    const sr_replica& r = c->reps[b];
+    if (cr.L != r.L || cr.rates != r.rates || cr.seed != r.seed || cr.J != r.J || cr.h != r.h ||
+        cr.T != r.T || !(cr.t_c >= 0.0) || !std::isfinite(cr.t_c))
+      return false;
+  }
+  return true;
+}
+
+int ckpt_load(sr_ctx* c, const unsigned char* in) {
+  const size_t nr = (size_t)c->NR, H = (size_t)c->prm.region_h;
+  in += sizeof(CkptHeader);
+  std::vector<CkptRep> cr((size_t)c->nrep);
+  std::memcpy(cr.data(), in, cr.size() * sizeof(CkptRep));
+  in += cr.size() * sizeof(CkptRep);
+  int rc = ckpt_push(c, c->rows, H, in);
+  if (rc == SR_OK) rc = ckpt_push(c, c->ci, 1, in);
+  if (rc == SR_OK) rc = ckpt_push(c, c->cx, 1, in);
+  if (rc == SR_OK) rc = ckpt_push(c, c->ckv, 1, in);
+  if (rc == SR_OK) rc = ckpt_push(c, c->cb, 1, in);
+  if (rc == SR_OK) rc = ckpt_push(c, c->ct, 1, in);
+  if (rc == SR_OK) rc = ckpt_push(c, c->cim, 1, in);
+  if (rc == SR_OK) rc = ckpt_push(c, c->cib, 1, in);
+  if (rc == SR_OK && c->prm.score) rc = ckpt_push(c, c->sc, 10, in);
+  if (rc == SR_OK && c->prm.score) rc = ckpt_push(c, c->si, 10, in);
+  if (rc != SR_OK) return rc;
+  std::vector<RepStats> rs((size_t)c->nrep);
+  for (int b = 0; b < c->nrep; ++b) rs[(size_t)b] = cr[(size_t)b].rs;
+  // copy 0 is the committed one everywhere; the rings refill from the
+  // committed event index at the next launch; no history is pending
+  if (cudaMemsetAsync(c->rcidx, 0, nr, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->rhi, 0, nr * sizeof(unsigned long long), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->hl, 0, 2 * 4 * nr * sizeof(uint32_t), c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->rs, rs.data(), rs.size() * sizeof(RepStats), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  KParams k = make_params(c);
+  halo_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, c->stream>>>(k);
+  c->launches += 1;
+  rc = cuda_rc(cudaGetLastError());
+  if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
+  if (rc != SR_OK) return rc;
+  for (int b = 0; b < c->nrep; ++b) {
+    c->t_c[b] = cr[(size_t)b].t_c;
+    c->wins[b] = cr[(size_t)b].wins;
+  }
+  c->last_nwin = 0;
+  return SR_OK;
+}
+
 // The last n entries of row `which` (0 iterations, 1 f) of the per-window ring.
 int window_ring(sr_ctx* c, int which, uint32_t* out, size_t n) {
   if (!c || !out) return SR_EINVAL;
@@ -1268,6 +1436,24 @@ int sr_score_grad(int n, int m, int nq, const double* A, const double* gA, const
   if (rc == SR_OK) rc = cuda_rc(cudaStreamSynchronize(st));
   cudaFree(sums);
   return rc;
+}
+
+int sr_checkpoint_size(sr_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return SR_EINVAL;
+  *bytes = ckpt_bytes(c);
+  return SR_OK;
+}
+
+int sr_checkpoint_save(sr_ctx* c, void* buf, size_t bytes) {
+  if (!c || !buf || bytes != ckpt_bytes(c)) return SR_EINVAL;
+  return ckpt_save(c, (unsigned char*)buf);
+}
+
+int sr_checkpoint_load(sr_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf || bytes != ckpt_bytes(c)) return SR_EINVAL;
+  const unsigned char* in = (const unsigned char*)buf;
+  if (!ckpt_matches(c, in)) return SR_EINVAL;
+  return ckpt_load(c, in);
 }
 
 int sr_get_info(sr_ctx* c, int* n_regions, int* frac_bits, uint64_t* P, int* threads_per_block,

@@ -173,7 +173,10 @@ def test_single_region_is_the_serial_n_fold_way():
 
 def test_iterations_follow_the_canonical_assumption():
     """Iteration 1 assumes no neighbour flips (§5): a window with no boundary
-    event converges in one iteration, any boundary event forces a second."""
+    event converges in one iteration, any boundary event forces a second.
+    Each iteration settles at least the next boundary event in time order
+    (the events before it see correct inputs), so a window with B boundary
+    events converges in at most B + 1 iterations."""
     lat = sr.Lattice(64, 1.0, 0.05, 1.5, (16, 16), seed=2, trace_capacity=1 << 12)
     lat.run_windows(1.0, 5)
     g = lat.window_iters()
@@ -187,6 +190,7 @@ def test_iterations_follow_the_canonical_assumption():
             sel = (times[q, :n] >= w) & (times[q, :n] < w + 1)
             nb += int(on_edge[q, :n][sel].sum())
         assert (g[w] == 1) == (nb == 0), (w, g[w], nb)
+        assert g[w] <= nb + 1, (w, g[w], nb)
 
 
 @pytest.mark.parametrize("lpr", LPR)
