@@ -58,10 +58,11 @@ HBM_GBS = 6788.3
 #       --clock-control none -k regex:relax_kernel -s 3 -c 1 \
 #       python bench.py --profile-case --tw TW --windows 100/TW
 # valid only for the kernel sources they were taken on (hash below; carried
-# over host-only additions to sr_lib.cu and sr.h -- the checkpoint calls --
-# with identical resource usage reported by ptxas for every kernel)
+# over host-only changes to sr_lib.cu and sr.h -- the checkpoint calls, the
+# wording of the timeout -- with identical resource usage reported by ptxas
+# for every kernel)
 TRAFFIC_BYTES = {0.25: 3482112 + 4785152, 1.0: 27091456 + 77085440, 4.0: 408394496 + 842041600}
-TRAFFIC_SOURCES_SHA = "ef51161e7b9263b6"
+TRAFFIC_SOURCES_SHA = "6b70cf6667816189"
 
 
 def _kernel_sources_sha():

@@ -39,7 +39,8 @@ extern "C" {
 #define SR_ECUDA (-3)           /* a CUDA call failed */
 #define SR_NOT_CONVERGED (-4)   /* iteration cap reached before a fixed point (§4, "UNTIL") */
 #define SR_CAPACITY (-5)        /* boundary history larger than the largest allowed capacity */
-#define SR_TIMEOUT (-6)         /* a grid-wide synchronize waited longer than its limit */
+#define SR_TIMEOUT (-6)         /* a bounded wait ran out: a grid-wide synchronize, or no task
+                                   published for a whole limit (asynchronous schedule) */
 #define SR_EUNSUPPORTED (-7)    /* valid but not supported by this build (e.g. region wider than 32) */
 #define SR_ETOOLARGE (-8)       /* problem needs more than the fixed scratch of sr_run_noalloc */
 
@@ -77,7 +78,9 @@ typedef struct sr_params {
   int threads_per_block;        /* region slots per block (lanes, or warps with a warp per
                                    region); 0 = automatic */
   int blocks;                   /* 0 = automatic (all regions resident if they fit) */
-  int barrier_timeout_ms;       /* bound on each grid-wide wait; 0 = 2000 */
+  int barrier_timeout_ms;       /* bound on each wait of the relaxation kernel (a grid-wide
+                                   synchronize; with the asynchronous schedule, a stretch with
+                                   no task published); 0 = 2000 */
   int replay_records;           /* incremental replay (one lane per region): checkpoints kept per
                                    region of the break points consumed in a pass, so the next pass
                                    restarts after its last unchanged input; 0 = 64, -1 = off */

@@ -1032,7 +1032,7 @@ const char* sr_strerror(int code) {
     case SR_ECUDA: return "CUDA error";
     case SR_NOT_CONVERGED: return "relaxation did not converge within the iteration cap";
     case SR_CAPACITY: return "boundary history exceeded the largest capacity";
-    case SR_TIMEOUT: return "grid-wide synchronize timed out";
+    case SR_TIMEOUT: return "a bounded wait of the relaxation kernel timed out";
     case SR_EUNSUPPORTED: return "unsupported configuration";
     case SR_ETOOLARGE: return "problem does not fit the fixed no-allocation scratch";
     default: return "unknown status";
