@@ -161,6 +161,9 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_checkpoint_size": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
             "sr_checkpoint_save": (C.c_int, [_P, _P, C.c_size_t]),
             "sr_checkpoint_load": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
+            "sr_run_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                         C.c_int, C.c_uint64, _P, C.c_double, C.c_int, _P, _P,
+                                         _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

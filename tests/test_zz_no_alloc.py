@@ -18,9 +18,7 @@ sr = pytest.importorskip("paper_cs_0405053_gb300")
 
 def _entry():
     fn = sr.library().sr_run_noalloc
-    fn.restype = C.c_int
-    fn.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_uint64,
-                   C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    assert fn.restype is C.c_int and len(fn.argtypes) == 13    # declared by the binding
     return fn
 
 
