@@ -269,10 +269,12 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
  * window, accumulated over windows in double).  The paper has no counterpart. */
 
 /* S[b][0..2] = d log L / d(beta, h, J) of each lattice b's committed path:
- * sum_k C_k d log p_k - sum_k I_k d p_k, with d log p_k of Metropolis
- * (0 where p_k = 1) or Glauber rates at the lattice's (J, h, T).  out: host,
- * 3 * n doubles.  Blocks.  Errors: SR_EINVAL, SR_EUNSUPPORTED (not score
- * mode), SR_ECUDA. */
+ * sum_k C_k d log p_k - sum_k I_k d p_k, with d log p_k of Metropolis or
+ * Glauber rates (Eqs. 2.2, 2.3) at the lattice's (J, h, T).  Metropolis:
+ * -d(beta dE) where dE > 0, 0 where dE < 0, and -d(beta dE) / 2 on the kink
+ * dE = 0 of min(1, exp(-beta dE)) (the mean of its left and right
+ * derivatives; e.g. the n_up = 2 classes at h = 0).  out: host, 3 * n doubles.
+ * Blocks.  Errors: SR_EINVAL, SR_EUNSUPPORTED (not score mode), SR_ECUDA. */
 int sr_score(sr_ctx* ctx, double* out);
 
 /* The statistics themselves for lattice `replica`, summed over its regions:

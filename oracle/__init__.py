@@ -171,9 +171,15 @@ def score_tables(J: float, h: float, T: float, glauber: bool = False):
     """d log p_k / d theta and d p_k / d theta for theta = (beta, h, J), beta =
     1/T, for the ten classes k = 5*[s=+1] + n_up (Eqs. 2.1-2.3): the flip of
     class k changes the energy by dE = 2 s (J (2 n_up - 4) + h).  Metropolis
-    p = min(1, exp(-beta dE)) has d log p = -d(beta dE) where dE > 0 and 0 where
-    dE <= 0 (p = 1 there); Glauber p = e / (1 + e), e = exp(-beta dE), has
-    d log p = -(1 - p) d(beta dE).  Returns (dlogp, dp), each [3, 10]."""
+    p = min(1, exp(-beta dE)) (Eq. 2.2) has d log p = -d(beta dE) where dE > 0
+    and 0 where dE < 0 (p = 1 there).  At dE = 0 p has a kink: moving theta_q
+    one way puts the class on the exp branch (one-sided derivative
+    -d(beta dE)/d theta_q), the other way on the p = 1 branch (derivative 0).
+    The table takes the mean of the two, -d(beta dE)/d theta_q / 2, so the
+    score's expectation is the mean of the left and right derivatives, which is
+    what a central difference measures.  Glauber p = e / (1 + e), e =
+    exp(-beta dE) (Eq. 2.3), is smooth: d log p = -(1 - p) d(beta dE).
+    Returns (dlogp, dp), each [3, 10]."""
     beta = 1.0 / T
     dlogp = np.zeros((3, 10))
     dp = np.zeros((3, 10))
@@ -187,6 +193,8 @@ def score_tables(J: float, h: float, T: float, glauber: bool = False):
             dlogp[:, k] = -(1.0 - p[k]) * d_bdE
         elif dE > 0.0:
             dlogp[:, k] = -d_bdE
+        elif dE == 0.0:                  # the kink of min(1, theta): both sides, averaged
+            dlogp[:, k] = -0.5 * d_bdE
         dp[:, k] = p[k] * dlogp[:, k]
     return dlogp, dp
 

@@ -119,8 +119,13 @@ void rate_table(const sr_replica& p, int F, unsigned long long P[10]) {
 // classes (Eqs. 2.1-2.3): a class-k flip changes the energy by
 // dE = 2 s (J (2 n_up - 4) + h), so d(beta dE) = (dE, 2 beta s, 2 beta s nb).
 // Metropolis, p = min(1, exp(-beta dE)): d log p = -d(beta dE) where dE > 0,
-// 0 where p = 1.  Glauber, p = e / (1 + e) with e = exp(-beta dE):
-// d log p = -(1 - p) d(beta dE).  tab = {dlog p [3][10], dp [3][10]}.
+// 0 where dE < 0 (p = 1).  At dE = 0 p has a kink, and a change of theta_q
+// puts the class on the exp branch on one side (derivative -d(beta dE)) and on
+// p = 1 on the other (derivative 0); the table holds their mean,
+// -d(beta dE) / 2, whose score expectation is the mean of the left and right
+// derivatives (what a central difference measures).  Glauber, p = e / (1 + e)
+// with e = exp(-beta dE): d log p = -(1 - p) d(beta dE).
+// tab = {dlog p [3][10], dp [3][10]}.
 void score_tables(const sr_replica& p, double* tab) {
   const double beta = 1.0 / p.T;
   for (int k = 0; k < 10; ++k) {
@@ -135,7 +140,7 @@ void score_tables(const sr_replica& p, double* tab) {
       if (p.rates == SR_RATES_GLAUBER)
         dl = -(1.0 - pk) * dx[q];
       else
-        dl = dE > 0.0 ? -dx[q] : 0.0;
+        dl = dE > 0.0 ? -dx[q] : (dE == 0.0 ? -0.5 * dx[q] : 0.0);
       tab[q * 10 + k] = dl;
       tab[30 + q * 10 + k] = pk * dl;
     }

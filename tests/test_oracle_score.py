@@ -77,3 +77,65 @@ def test_score_derivative_matches_exact_dynamics(J, h, T, glauber):
         (_exact_mean_m(J, h + d, T, glauber, t) - _exact_mean_m(J, h - d, T, glauber, t)) / (2 * d),
         (_exact_mean_m(J + d, h, T, glauber, t) - _exact_mean_m(J - d, h, T, glauber, t)) / (2 * d)])
     assert np.all(np.abs(est - exact) < 4.0 * se + 1e-6), (est, exact, se)
+
+
+def _exact_mean_m_start(J, h, T, t, init, L=3):
+    """E[M(t)] exactly for the Metropolis chain: from the all-up state, or from
+    fair-coin spins (every state equally likely)."""
+    S = _all_states(L)
+    M = S.sum(axis=1).astype(np.float64)
+    P = linalg.expm(_generator(L, J, h, T, False) * t)
+    if init == "up":
+        return float(P[int(np.argmax(M))] @ M)
+    return float(P.mean(axis=0) @ M)
+
+
+@pytest.mark.parametrize("init,T,t,n", [("up", 3.5, 3.0, 160000), ("fair", 2.5, 0.8, 40000)])
+def test_score_at_the_metropolis_kink(init, T, t, n):
+    """h = 0 puts the n_up = 2 classes exactly on the kink of Eq. 2.2
+    (dE = 2 s h = 0), where p = min(1, exp(-beta dE)) has different left and
+    right derivatives in h.  Pinned against the exact chain of the 3x3
+    lattice: the score built with the right-hand (left-hand) derivative at the
+    kink estimates the exact right (left) derivative of E[M(t)] in h, and the
+    table's mean of the two estimates the central difference.  From the all-up
+    state the left and right derivatives differ; from fair-coin spins they are
+    equal by symmetry, and a table that takes the right derivative for one
+    spin sign and the left for the other misses by tens of standard errors."""
+    J, h, beta = 1.0, 0.0, 1.0 / T
+    mode = oracle.INIT_ALL_UP if init == "up" else oracle.INIT_FAIR_COIN
+    ms, C, O = np.zeros(n), np.zeros((n, 10)), np.zeros((n, 10))
+    for i in range(n):
+        r = oracle.run(3, J, h, T, 3, 3, 1000 + i, [t], init_mode=mode, keep_spins=False,
+                       keep_counts=False)
+        ms[i] = r.mag[-1]
+        C[i] = r.ev_class.sum(axis=0)
+        O[i] = r.occupancy.sum(axis=0)
+    dlogp, dp = oracle.score_tables(J, h, T)
+    p = oracle.rates(J, h, T)
+    # the kink classes: s = -1 (k = 2) and s = +1 (k = 7) with two up neighbours
+    assert p[2] == 1.0 and p[7] == 1.0
+    assert dlogp[1, 7] == -beta and dlogp[1, 2] == beta       # mean of -2 beta | 0 and 0 | 2 beta
+    assert dlogp[0, 2] == dlogp[0, 7] == dlogp[2, 2] == dlogp[2, 7] == 0.0   # d(beta dE) = 0
+
+    def estimate(tab_h):
+        S = C @ tab_h - O @ (p * tab_h)
+        a = ms * S
+        return a.mean(), a.std() / math.sqrt(n)
+
+    d = 1e-6
+    e0 = _exact_mean_m_start(J, 0.0, T, t, init)
+    right = (_exact_mean_m_start(J, d, T, t, init) - e0) / d
+    left = (e0 - _exact_mean_m_start(J, -d, T, t, init)) / d
+    central = 0.5 * (right + left)
+    tab_right, tab_left, tab_mixed = dlogp[1].copy(), dlogp[1].copy(), dlogp[1].copy()
+    tab_right[7], tab_right[2] = -2 * beta, 0.0
+    tab_left[7], tab_left[2] = 0.0, 2 * beta
+    tab_mixed[7], tab_mixed[2] = 0.0, 0.0
+    for tab, want in ((dlogp[1], central), (tab_right, right), (tab_left, left)):
+        est, se = estimate(tab)
+        assert abs(est - want) < 4.0 * se + 1e-6, (init, est, want, se)
+    if init == "fair":
+        est, se = estimate(tab_mixed)
+        assert abs(est - central) > 20.0 * se, (est, central, se)
+    else:
+        assert right - left > 0.3          # a real kink: one-sided tables would be biased
