@@ -1,20 +1,26 @@
 """Benchmark: committed spin flips per second of the synchronous-relaxation
 n-fold-way Ising simulation on GB300.
 
-Workload (one "step" = the whole hot path over the lattice, for each window
-length): L = 1024 periodic 2D Ising, 64 x 64 regions of 16 x 16, J = 1,
-h = 0.05, T = 1.0, fair-coin initial spins from the seed; for each window
-length Tw in {0.25, 1, 4}: initialise (spins, class counts, first waiting
-times), run synchronous relaxation windows to t = 100, reduce the observables.
+Headline workload (one "step" = the whole hot path over the batch): 256
+independent periodic 2D Ising lattices, L uniform over {64, 128, 256, 512,
+1024}, T uniform in [1, 3.5], h uniform in [-0.2, 0.2], J = 1, fair-coin
+initial spins; region shape, region lanes per warp and events per window
+chosen by the autotuner; every lattice restarts from its initial state and
+runs to t = 100 with window lengths matched to its event rate, then its
+observables are reduced.  Beside it: the same lattices one per context (the
+"plain" form), the plain single-lattice workloads L = 1024 (window lengths
+0.25, 1, 4 to t = 100) and L = 8192 (window length 0.1 to t = 50), f and g
+of §6 against log N, and the oracle on a bounded sample of the batch.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 N > 1 is launched with torch.distributed.run: each rank simulates its own
-replica (seed 1 + rank) on its own GPU, with no data exchange ("scaling":
-"weak"); rank 0 prints one JSON line.
+batch (lattice b of rank r has seed 1000 + 256 r + b) on its own GPU, with no
+data exchange ("scaling": "weak"); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -29,11 +35,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "committed spin flips/s on 1 GB300 (batched vs plain), % roofline, iters"
 UNIT = "flips/s"
-L, RW, RH, J, H_FIELD, TEMP, T_END = 1024, 16, 16, 1.0, 0.05, 1.0, 100.0
-WINDOWS = (0.25, 1.0, 4.0)
-WORKLOAD = ("L=1024 periodic 2D Ising, 64x64 regions of 16x16, J=1, h=0.05, T=1.0, fair-coin "
-            "spins, Metropolis rates via the n-fold way, run to t=100 for each window length "
-            "Tw in {0.25, 1, 4}")
+T_END = 100.0
+BATCH_N = 256
+WORKLOAD = ("256 lattices: L uniform over {64,128,256,512,1024}, T uniform in [1,3.5], h uniform "
+            "in [-0.2,0.2], J=1, fair-coin spins, Metropolis rates via the n-fold way, run to "
+            "t=100 each (numpy Philox key 4, seeds 1000+b), autotuned region shape, adaptive "
+            "window lengths")
+PLAIN_L, PLAIN_W, PLAIN_H, PLAIN_T, PLAIN_WINDOWS = 1024, 0.05, 1.0, 100.0, (0.25, 1.0, 4.0)
 
 # Algorithmic work of the method per committed event (counted from the formulas
 # of §3 and §5, independent of how this implementation executes them):
@@ -47,22 +55,26 @@ OPS_PER_BREAK = 35
 # Integer issue peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz.
 SMS, LANES_PER_SM, SM_MHZ = 152, 128, 2070.0
 INT_PEAK_OPS = SMS * LANES_PER_SM * SM_MHZ * 1e6          # 4.03e13 lane-ops/s
+# FP64 pipe (measured on one GB300 with a probe of dependent-free DFMA / DDIV
+# streams): 5.0e11 DFMA lane-ops/s; one DDIV takes about 8.6 DFMA slots.
+# Per committed event the formulas need -log U (26 add/mul, 1 divide, 1
+# integer-to-double conversion) and the waiting time (Lambda conversion and
+# scale, subtract, divide, add: 4 add/mul/convert, 1 divide): 32 slots + 2
+# divides = 49 DFMA slots.
+FP64_PEAK_OPS = 5.0e11
+FP64_SLOTS_PER_EVENT = 32 + 2 * 8.6
 # History bytes per committed boundary event: f64 time + u8 position, written
-# once and read by one neighbour (two for a corner); the HBM bound uses the
-# measured copy bandwidth of this part.
+# once and read by one neighbour (two for a corner).
 HIST_BYTES_PER_BOUNDARY_EVENT = 9 * 2
-HBM_GBS = 6788.3
-# DRAM bytes (read + write) of one relaxation launch of each window length,
-# from one ncu capture of the full launch on a GB300:
-#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
-#       --clock-control none -k regex:relax_kernel -s 3 -c 1 \
-#       python bench.py --profile-case --tw TW --windows 100/TW
-# valid only for the kernel sources they were taken on (hash below; carried
-# over host-only changes to sr_lib.cu and sr.h -- the checkpoint calls, the
-# wording of the timeout -- with identical resource usage reported by ptxas
-# for every kernel)
-TRAFFIC_BYTES = {0.25: 3482112 + 4785152, 1.0: 27091456 + 77085440, 4.0: 408394496 + 842041600}
-TRAFFIC_SOURCES_SHA = "6b70cf6667816189"
+HBM_GBS_FALLBACK = 6800.0
+# DRAM bytes (read + write) per relaxation launch of the batched step, mean
+# over the launches of one whole step (one ncu capture on a GB300; the
+# configuration and command are in profiles/); valid only for the kernel
+# sources they were taken on (hash below) and for the same tuning.
+BATCH_TRAFFIC = None            # {"bytes_per_launch": B, "tuning": [W, H, lpw, kappa]}
+BATCH_TRAFFIC_SHA = None
+PLAIN_TRAFFIC = None            # {Tw: bytes per launch} of the L = 1024 launches
+PLAIN_TRAFFIC_SHA = None
 
 
 def _kernel_sources_sha():
@@ -75,6 +87,27 @@ def _kernel_sources_sha():
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- rank bookkeeping
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def rank_seed0(rank):
+    """First seed of the batch a rank simulates (each rank its own lattices)."""
+    return 1000 + BATCH_N * rank
 
 
 def job_throughput(dist, seconds, committed, device):
@@ -90,18 +123,33 @@ def job_throughput(dist, seconds, committed, device):
     return t_max, float(c.item()) / t_max
 
 
-def replica_seed(rank):
-    """Seed of the lattice simulated by a rank (each rank its own replica)."""
-    return 1 + rank
+def timed_steps(step, steps, warmup, dist=None, sync=lambda: None, between=lambda: None):
+    """W untimed warm-up steps, then exactly K timed steps bracketed by a
+    barrier and a synchronize on both sides.  `step()` returns (seconds,
+    units) of one step as measured by the caller (CUDA events on the GPU);
+    `between()` runs before each timed step, outside its measurement (the L2
+    flush).  Returns (per-step seconds, units, wall seconds of the loop)."""
+    for _ in range(warmup):
+        step()
+    sync()
+    if dist is not None:
+        dist.barrier()
+    sync()
+    secs, units = [], 0
+    w0 = time.perf_counter()
+    for _ in range(steps):
+        between()
+        s, u = step()
+        secs.append(s)
+        units += u
+    sync()
+    if dist is not None:
+        dist.barrier()
+    sync()
+    return secs, units, time.perf_counter() - w0
 
 
-def _dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
-
-
+# ---------------------------------------------------------------- clocks
 def _clock_sampler(path):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -137,125 +185,189 @@ def _clock_summary(path, gpu_index):
             "samples": len(sm)}
 
 
-def _oracle_baseline(Tw=1.0):
-    """The oracle (plain sequential C) on the workload for one window length:
-    the lattice to t = 100 with window ends every Tw."""
+# ---------------------------------------------------------------- the oracle (CPU baseline)
+def _oracle_job(args):
+    """One oracle run (plain sequential C, one core): lattice `rep` from t = 0
+    to t_end.  Returns (committed events, seconds)."""
     import oracle
-    oracle.build()
-    n = int(round(T_END / Tw))
-    ends, t = [], 0.0
-    for _ in range(n):
-        t = t + Tw
-        ends.append(t)
+    rep, t_end = args
     t0 = time.perf_counter()
-    r = oracle.run(L, J, H_FIELD, TEMP, RW, RH, 1, ends, keep_spins=False)
-    dt = time.perf_counter() - t0
-    committed = int(r.counts[-1].sum())
-    return committed, dt
+    r = oracle.run(rep["L"], rep["J"], rep["h"], rep["T"], rep["W"], rep["H"], rep["seed"],
+                   [t_end], keep_spins=False)
+    return int(r.counts[-1].sum()), time.perf_counter() - t0
+
+
+def _oracle_pool(n):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(n)
+
+
+def oracle_sample(reps, region, rates, events_per_job=3.0e6):
+    """A bounded sample of the batched workload for the oracle: a stratified
+    set of lattices (every side L, cold to hot), each run from t = 0 to the
+    time at which it has committed about `events_per_job` events at its own
+    event rate `rates[b]` (events per unit time), at most t = 100."""
+    from paper_cs_0405053_gb300 import workloads
+    jobs = []
+    for b in workloads.stratified(reps, per_side=3):
+        t_end = min(T_END, max(0.25, events_per_job / max(rates[b], 1.0)))
+        rep = dict(reps[b], W=region[0], H=region[1])
+        jobs.append((rep, float(t_end)))
+    return jobs
+
+
+def run_oracle_sample(pool, jobs):
+    """(committed, wall seconds, per-core events/s) of the jobs run in parallel."""
+    w0 = time.perf_counter()
+    res = pool.map(_oracle_job, jobs, chunksize=1)
+    wall = time.perf_counter() - w0
+    committed = sum(c for c, _ in res)
+    per_core = committed / max(1e-9, sum(s for _, s in res))
+    return committed, wall, per_core
+
+
+def _calibrated_rates(pool, reps, region):
+    """Events per unit time of every sampled lattice from a short oracle run
+    (t = 0.25), for sizing the reference arm's sample."""
+    from paper_cs_0405053_gb300 import workloads
+    idx = workloads.stratified(reps, per_side=3)
+    res = pool.map(_oracle_job, [(dict(reps[b], W=region[0], H=region[1]), 0.25) for b in idx],
+                   chunksize=1)
+    rates = {b: c / 0.25 for b, (c, _) in zip(idx, res)}
+    return [rates.get(b, 1.0) for b in range(len(reps))]
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the plain CPU simulation the GPU path is
+    checked against) timed on this machine's cores on the headline workload,
+    each step a bounded sample of it (see oracle_sample)."""
     rank, world, _ = _dist_env()
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        _oracle_baseline(WINDOWS[0])
-    times, committed = [], 0
-    for _ in range(args.steps):
-        step_t = 0.0
-        for Tw in WINDOWS:                     # one oracle run per window length, as a step
-            c, dt = _oracle_baseline(Tw)
+    from paper_cs_0405053_gb300 import workloads
+    reps = workloads.batch_replicas()
+    region = (32, 16)
+    cores = max(1, min(os.cpu_count() or 1, 16))
+    pool = _oracle_pool(cores)
+    try:
+        rates = _calibrated_rates(pool, reps, region)
+        jobs = oracle_sample(reps, region, rates, events_per_job=1.5e6)
+        for _ in range(args.warmup):
+            run_oracle_sample(pool, jobs[:cores])
+        committed, secs = 0, 0.0
+        for _ in range(args.steps):
+            c, s, _ = run_oracle_sample(pool, jobs)
             committed += c
-            step_t += dt
-        times.append(step_t)
-    total = sum(times)
-    value = committed / total
+            secs += s
+    finally:
+        pool.terminate()
+        pool.join()
+    value = committed / secs
+    sample = (f"per step {len(jobs)} lattices of the batch (3 per side L: coldest, median, "
+              f"hottest), each from t=0 until about 1.5e6 committed events (at most t=100), "
+              f"region {region[0]}x{region[1]}, one oracle process per core")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
         "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "the full workload: per step one oracle run to t=100 for each "
-                                   "window length (0.25, 1, 4), every committed flip counted once"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _batched_vs_plain(args, sr, torch, stream):
-    """The batched workload: 256 independent lattices (L uniform over
-    {64 .. 1024}, T uniform in [1, 3.5], h uniform in [-0.2, 0.2], J = 1,
-    fair-coin spins) run to t = args.batch_t in one context, with the region
-    shape, lanes per warp and events per window chosen by the autotuner and
-    window lengths matched to each lattice's event rate; against the same
-    lattices run one per context (a stratified sample of every 8th lattice)."""
-    from paper_cs_0405053_gb300 import workloads
-    reps = workloads.batch_replicas()
-    t0 = time.perf_counter()
-    tune = sr.autotune(reps, t_trial=1.0)
-    tune_s = time.perf_counter() - t0
-    t_end = float(args.batch_t)
-
-    def timed(b, lpw):
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+# ---------------------------------------------------------------- our arm
+def _plain_L1024(sr, torch, stream):
+    """The plain single-lattice workload: L = 1024 in 16 x 16 regions, J = 1,
+    h = 0.05, T = 1, fair coin; for each window length 0.25, 1, 4: restart,
+    windows to t = 100, observables (one persistent launch per window set)."""
+    lat = sr.Lattice(PLAIN_L, 1.0, PLAIN_W, PLAIN_H, (16, 16), seed=1)
+    out, com, dev = {}, 0, 0.0
+    for Tw in PLAIN_WINDOWS:
+        n = int(round(PLAIN_T / Tw))
+        lat.reset()
+        o0 = lat.observables()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        lat.run_windows(Tw, n)
+        o = lat.observables()
+        ev[1].record(stream)
         torch.cuda.synchronize()
-        w0 = time.perf_counter()
-        ev0.record(stream)
-        b.run_adaptive(t_end, kappa=tune.kappa)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - w0
-        obs = [b.observables(k) for k in range(len(b))]
-        return ev0.elapsed_time(ev1) * 1e-3, wall, obs
+        ms = ev[0].elapsed_time(ev[1])
+        it = [int(v) for v in lat.window_iters(n)]
+        kms = o.relax_ms - o0.relax_ms
+        out[str(Tw)] = {"ms": round(ms, 3), "kernel_ms": round(kms, 3), "committed": o.committed,
+                        "generated": o.generated,
+                        "wasted_ratio": (o.generated - o.committed) / max(1, o.committed),
+                        "iters_mean": statistics.mean(it) if it else None,
+                        "iters_max": max(it) if it else None, "max_f": o.max_f,
+                        "breaks": o.breaks, "flips_per_s": o.committed / (ms * 1e-3)}
+        com += o.committed
+        dev += ms * 1e-3
+    kms_all = sum(v["kernel_ms"] for v in out.values())
+    ops = com * OPS_PER_EVENT / (kms_all * 1e-3)
+    lat.close()
+    return {"workload": "L=1024 periodic, 64x64 regions of 16x16, J=1, h=0.05, T=1.0, fair-coin "
+                        "spins, Tw in {0.25, 1, 4} to t=100 (one persistent launch each)",
+            "flips_per_s": com / dev, "per_window_length": out,
+            "roofline": {"bound": "alu", "kernel": "relax_kernel<0,0>", "achieved": ops / 1e12,
+                         "peak": INT_PEAK_OPS / 1e12, "unit": "Tops/s", "frac": ops / INT_PEAK_OPS,
+                         "traffic": (statistics.mean(PLAIN_TRAFFIC.values())
+                                     if PLAIN_TRAFFIC and _kernel_sources_sha() == PLAIN_TRAFFIC_SHA
+                                     else None)}}
 
-    bt = sr.Batch(reps, region=tune.region, lanes_per_warp=tune.lanes_per_warp)
-    bt.run_adaptive(min(1.0, t_end), kappa=tune.kappa)      # warm-up
-    bt.reset()
-    clock_path = os.path.join(tempfile.gettempdir(), f"sr_clocks_batch_{os.getpid()}.csv")
-    sampler = _clock_sampler(clock_path)
-    time.sleep(0.3 if sampler else 0)
-    dev_s, wall_s, obs = timed(bt, tune.lanes_per_warp)
-    if sampler:
-        sampler.terminate()
-        sampler.wait()
-    committed = sum(o.committed for o in obs)
-    generated = sum(o.generated for o in obs)
-    iters = sum(o.iterations for o in obs) / max(1, sum(o.windows for o in obs))
-    launches = obs[0].launches
-    bt.close()
-    batched = committed / dev_s
 
-    sample = list(range(0, len(reps), 8))
-    p_com, p_s = 0, 0.0
+def _plain_L8192(sr, torch, stream, t_end=50.0):
+    """The plain method at scale: L = 8192 in 256 x 256 regions of 32 x 32,
+    J = 1, h = 0, T = 2.269, fair coin, window length 0.1 to t = 50."""
+    lat = sr.Lattice(8192, 1.0, 0.0, 2.269, (32, 32), seed=1, init="fair")
+    n = int(round(t_end / 0.1))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    lat.run_windows(0.1, n)
+    o = lat.observables()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    s = ev[0].elapsed_time(ev[1]) * 1e-3
+    it = lat.window_iters(n)
+    lat.close()
+    ops = o.committed * OPS_PER_EVENT / (o.relax_ms * 1e-3)
+    return {"workload": f"L=8192 periodic, 256x256 regions of 32x32, J=1, h=0, T=2.269, fair-coin "
+                        f"spins, Tw=0.1 to t={t_end:g}",
+            "flips_per_s": o.committed / s, "s": s, "committed": o.committed,
+            "wasted_ratio": (o.generated - o.committed) / max(1, o.committed),
+            "iters_mean": float(it.mean()) if len(it) else None, "max_f": o.max_f,
+            "roofline": {"bound": "alu", "kernel": "relax_kernel<0,1>", "achieved": ops / 1e12,
+                         "peak": INT_PEAK_OPS / 1e12, "unit": "Tops/s",
+                         "frac": ops / INT_PEAK_OPS}}
+
+
+def _one_by_one(sr, torch, stream, reps, tune, every=16):
+    """The plain form of the batched workload: a stratified sample of the
+    lattices (every `every`-th), each in its own context with the same region
+    shape and window rule, run one after the other."""
+    com, dev = 0, 0.0
+    sample = list(range(0, len(reps), every))
     for k in sample:
         one = sr.Batch([reps[k]], region=tune.region)
-        d, _, o = timed(one, 0)
-        p_com += o[0].committed
-        p_s += d
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        one.run_adaptive(T_END, kappa=tune.kappa)
+        o = one.observables(0)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        com += o.committed
+        dev += ev[0].elapsed_time(ev[1]) * 1e-3
         one.close()
-    plain = p_com / p_s
-    ops = committed * OPS_PER_EVENT / dev_s
-    return {
-        "workload": "256 lattices: L uniform over {64,128,256,512,1024}, T uniform in [1,3.5], "
-                    "h uniform in [-0.2,0.2], J=1, fair-coin spins, Metropolis, run to "
-                    f"t={t_end:g} each (numpy Philox key 4, seeds 1000+b)",
-        "sites": int(sum(r["L"] ** 2 for r in reps)),
-        "tuning": {"region": list(tune.region), "lanes_per_warp": tune.lanes_per_warp or "auto",
-                   "kappa": tune.kappa, "trials": tune.trials, "seconds": round(tune_s, 2)},
-        "batched": {"flips_per_s": batched, "s": dev_s, "wall_s": wall_s, "committed": committed,
-                    "generated": generated, "wasted_ratio": (generated - committed) / committed,
-                    "iters_mean": iters, "launches": launches},
-        "one_by_one": {"flips_per_s": plain, "s": p_s, "committed": p_com,
-                       "sample": f"every 8th lattice ({len(sample)} of {len(reps)}), each in its "
-                                 "own context with the same shape and window rule"},
-        "batched_over_one_by_one": batched / plain,
-        "clocks": _clock_summary(clock_path, torch.cuda.current_device()),
-        "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": INT_PEAK_OPS / 1e12,
-                     "unit": "Tops/s", "frac": ops / INT_PEAK_OPS},
-    }
+    return {"flips_per_s": com / dev, "s": dev, "committed": com,
+            "sample": f"every {every}th lattice ({len(sample)} of {len(reps)}), each in its own "
+                      "context with the same region shape and window rule"}
 
 
 def _fg_vs_log_n(sr):
@@ -264,9 +376,9 @@ def _fg_vs_log_n(sr):
     lambda = 1, 60 boundary sites); 20 windows of warm-up, 60 measured."""
     rows = []
     for L in (64, 128, 256, 512, 1024, 2048):
-        N = (L // RW) ** 2
+        N = (L // 16) ** 2
         Tw = math.log(N) / 60.0
-        lat = sr.Lattice(L, 1.0, 0.0, 3.0, (RW, RH), seed=7)
+        lat = sr.Lattice(L, 1.0, 0.0, 3.0, (16, 16), seed=7)
         lat.run_windows(Tw, 20)
         o0 = lat.observables()
         t0 = time.perf_counter()
@@ -290,6 +402,7 @@ def run_ours(args):
     import torch
 
     import paper_cs_0405053_gb300 as sr
+    from paper_cs_0405053_gb300 import workloads
 
     rank, world, local = _dist_env()
     if not torch.cuda.is_available():
@@ -299,148 +412,166 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    seed = replica_seed(rank)
     stream = torch.cuda.current_stream()
-    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr,
-                     lanes_per_warp=args.lpw, time_arith=args.arith)
+    reps = workloads.batch_replicas(seed0=rank_seed0(rank))
+    t0 = time.perf_counter()
+    tune = sr.autotune(reps, t_trial=1.0)
+    tune_s = time.perf_counter() - t0
+    bt = sr.Batch(reps, region=tune.region, lanes_per_warp=tune.lanes_per_warp)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    n = len(reps)
 
-    def one_pass(record):
-        """One step: for each window length, init + windows to t=100 + observables."""
-        out = []
-        for Tw in WINDOWS:
-            n = int(round(T_END / Tw))
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            ev[0].record(stream)
-            lat.reset()
-            ev[1].record(stream)
-            lat.run_windows(Tw, n)
-            ev[2].record(stream)
-            obs = lat.observables()
-            ev[3].record(stream)
-            out.append((Tw, ev, obs, lat.window_iters(n)))
-        return out
-
-    for _ in range(args.warmup):
-        one_pass(False)
-    torch.cuda.synchronize()
+    def step():
+        """The whole hot path over the batch: every lattice restarts from its
+        initial state, runs to t = 100, and its observables are reduced."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        bt.reset()
+        bt.run_adaptive(T_END, kappa=tune.kappa)
+        obs = [bt.observables(b) for b in range(n)]
+        ev[1].record(stream)
+        ev[1].synchronize()
+        step.last = obs
+        return ev[0].elapsed_time(ev[1]) * 1e-3, sum(o.committed for o in obs)
 
     clock_path = os.path.join(tempfile.gettempdir(), f"sr_clocks_{os.getpid()}.csv")
+    for _ in range(args.warmup):
+        step()
+    o_before = bt.observables(0)
     sampler = _clock_sampler(clock_path) if rank == 0 else None
     time.sleep(0.3 if sampler else 0)
-    step_ms, kernel_ms, per_tw = [], [], {Tw: [] for Tw in WINDOWS}
-    committed_total = 0
-    launches0 = lat.observables().launches
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()                         # L2 flush between timed steps (outside the events)
-        res = one_pass(True)
-        torch.cuda.synchronize()
-        ms = 0.0
-        for Tw, ev, obs, iters in res:
-            ms += ev[0].elapsed_time(ev[3])
-            kernel_ms.append(ev[1].elapsed_time(ev[2]))
-            committed_total += obs.committed          # counters restart at each reset
-            launches_last = obs.launches
-            per_tw[Tw].append((ev[0].elapsed_time(ev[3]), ev[1].elapsed_time(ev[2]), obs, iters))
-        step_ms.append(ms)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    wall = time.perf_counter() - wall0
-    launches = launches_last - launches0
+    secs, committed, wall = timed_steps(step, args.steps, 0, dist, torch.cuda.synchronize,
+                                        flush.zero_)
     if sampler:
         sampler.terminate()
         sampler.wait()
-    total_ms = sum(step_ms)
-    t_max, value = job_throughput(dist, total_ms / 1e3, committed_total, "cuda")
+    o_after = bt.observables(0)
+    t_max, value = job_throughput(dist, sum(secs), committed, "cuda")
+    obs = step.last
+    generated = sum(o.generated for o in obs)
+    com_step = sum(o.committed for o in obs)
+    iters = sum(o.iterations for o in obs) / max(1, sum(o.windows for o in obs))
+    relax_ms = o_after.relax_ms - o_before.relax_ms
+    relax_n = o_after.relax_launches - o_before.relax_launches
+    launches = (o_after.launches - o_before.launches) // max(1, args.steps)
 
-    # ---- end to end through the public API with host buffers: upload the
-    # initial spins from pinned memory, run, read back observables and spins
-    rng = np.random.default_rng(1000 + rank)
-    init_host = torch.from_numpy(np.where(rng.random((L, L)) < 0.5, 1, -1).astype(np.int8)).pin_memory()
-    out_host = torch.empty((L, L), dtype=torch.int8).pin_memory()
-    e2e_lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=seed, lanes_per_region=args.lpr,
-                         lanes_per_warp=args.lpw, time_arith=args.arith)
-    e2e_committed, e2e_time = 0, 0.0
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        c_step = 0
-        for Tw in WINDOWS:
-            e2e_lat.set_spins(init_host.numpy())
-            e2e_lat.run_windows(Tw, int(round(T_END / Tw)))
-            o = e2e_lat.observables()
-            sr.library().sr_get_spins(e2e_lat._ctx, out_host.data_ptr(), L * L)
-            c_step += o.committed
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            e2e_committed += c_step
-            e2e_time += dt
-    e2e_lat.close()
-    e2e_value = e2e_committed / e2e_time if e2e_time > 0 else None
+    # ---- end to end through the public API with host buffers: every step
+    # uploads each lattice's initial spins from pinned memory (a fair coin of
+    # numpy's PCG64 from seed 2000 + b), runs it to t = 100 and reads back the
+    # final spins and observables
+    sites = [r["L"] ** 2 for r in reps]
+    offs = np.concatenate([[0], np.cumsum(sites)])
+    rng = np.random.default_rng(2000 + rank)
+    init_host = torch.from_numpy(
+        np.where(rng.random(int(offs[-1])) < 0.5, 1, -1).astype(np.int8)).pin_memory()
+    out_host = torch.empty(int(offs[-1]), dtype=torch.int8).pin_memory()
+    base_in, base_out = init_host.data_ptr(), out_host.data_ptr()
+
+    def e2e_step():
+        w0 = time.perf_counter()
+        for b in range(n):
+            bt.set_spins(b, base_in + int(offs[b]))
+        bt.run_adaptive(T_END, kappa=tune.kappa)
+        c = 0
+        for b in range(n):
+            bt.spins_into(b, base_out + int(offs[b]))
+            c += bt.observables(b).committed
+        return time.perf_counter() - w0, c
+
+    e2e_steps = max(3, args.steps // 4)
+    e_secs, e_com, _ = timed_steps(e2e_step, e2e_steps, 1, dist, torch.cuda.synchronize)
+    _, e2e_value = job_throughput(dist, sum(e_secs), e_com, "cuda")
+    launch_shape = {"blocks": bt.blocks, "region_slots_per_block": bt.threads_per_block}
+    bt.close()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (the persistent relaxation kernel):
-    # algorithmic integer work of the committed trajectory per launch / launch time
-    kms = sum(kernel_ms) / len(kernel_ms)
-    last = {Tw: per_tw[Tw][-1] for Tw in WINDOWS}
-    ev_per_launch = statistics.mean(o.committed for (_, _, o, _) in (last[t] for t in WINDOWS))
-    ops = ev_per_launch * OPS_PER_EVENT
-    achieved = ops / (kms * 1e-3)
-    peak = INT_PEAK_OPS
-    # the other bound of the statement: boundary history bytes at HBM bandwidth
-    # (boundary fraction of 16x16 regions at uniform rates, 60/256)
-    hbm_bound_events = HBM_GBS * 1e9 / (HIST_BYTES_PER_BOUNDARY_EVENT * 60 / 256)
-    cpu_committed, cpu_dt = _oracle_baseline()
-    batch_info = None if args.no_batch else _batched_vs_plain(args, sr, torch, stream)
-    fg_rows = None if args.no_batch else _fg_vs_log_n(sr)
-    tw_detail = {}
-    for Tw in WINDOWS:
-        ms, kms_tw, o, iters = per_tw[Tw][-1]
-        it = [int(v) for v in iters]
-        tw_detail[str(Tw)] = {
-            "ms": round(ms, 3), "kernel_ms": round(kms_tw, 3), "committed": o.committed,
-            "generated": o.generated, "wasted_ratio": (o.generated - o.committed) / max(1, o.committed),
-            "iters_mean": statistics.mean(it) if it else None, "iters_max": max(it) if it else None,
-            "windows": len(it), "max_f": o.max_f, "breaks": o.breaks,
-            "flips_per_s": o.committed / (ms * 1e-3)}
+    # ---- the plain forms and the measurement context (rank 0)
+    one = _one_by_one(sr, torch, stream, reps, tune)
+    plain_1024 = _plain_L1024(sr, torch, stream)
+    plain_8192 = _plain_L8192(sr, torch, stream)
+    fg_rows = _fg_vs_log_n(sr)
+
+    # ---- the oracle on a bounded sample of the batch, one process per core,
+    # each lattice sized by its event rate in the GPU run
+    rates = [o.committed / T_END for o in obs]
+    cores = max(1, min(os.cpu_count() or 1, 16))
+    pool = _oracle_pool(cores)
+    try:
+        jobs = oracle_sample(reps, tune.region, rates)
+        cpu_com, cpu_wall, cpu_per_core = run_oracle_sample(pool, jobs)
+    finally:
+        pool.terminate()
+        pool.join()
+
+    # ---- roofline of the dominant kernel (the batched relaxation launches):
+    # algorithmic integer work of the committed trajectory per launch over the
+    # launch's CUDA-event time
+    per_launch_ms = relax_ms / max(1, relax_n)
+    ev_per_launch = committed / max(1, relax_n)
+    achieved = ev_per_launch * OPS_PER_EVENT / (per_launch_ms * 1e-3)
+    peaks = _measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_GBS_FALLBACK))
+    W, H = tune.region
+    phi = (2 * W + 2 * H - 4) / (W * H)                 # boundary sites of a region
+    ev_rate = committed / (relax_ms * 1e-3)
+    bounds = {"integer_issue": INT_PEAK_OPS / OPS_PER_EVENT,
+              "history_bytes_at_hbm": hbm * 1e9 / (HIST_BYTES_PER_BOUNDARY_EVENT * phi),
+              "fp64_pipe": FP64_PEAK_OPS / FP64_SLOTS_PER_EVENT}
+    traffic = None
+    if (BATCH_TRAFFIC and _kernel_sources_sha() == BATCH_TRAFFIC_SHA and
+            BATCH_TRAFFIC["tuning"] == [W, H, tune.lanes_per_warp, tune.kappa]):
+        traffic = BATCH_TRAFFIC["bytes_per_launch"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded fair-coin lattice)",
-        "config": {"workload": WORKLOAD, "regions": lat.n_regions,
-                   "launch": {"region_slots_per_block": lat.threads_per_block, "blocks": lat.blocks,
-                              "lanes_per_region": args.lpr or "auto"},
-                   "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "per_window_length": tw_detail},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                     "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": (statistics.mean(TRAFFIC_BYTES[t] for t in WINDOWS)
-                                 if _kernel_sources_sha() == TRAFFIC_SOURCES_SHA else None),
-                     "traffic_unit": "bytes per launch (DRAM read + write, mean over the "
-                                     "three window lengths; ncu)",
+        "data": "synthetic (seeded lattices, fair-coin spins)",
+        "config": {"workload": WORKLOAD, "lattices": n, "sites": int(offs[-1]),
+                   "tuning": {"region": list(tune.region),
+                              "lanes_per_warp": tune.lanes_per_warp or "auto",
+                              "kappa": tune.kappa, "trials": tune.trials,
+                              "seconds": round(tune_s, 2)},
+                   "launch": launch_shape,
+                   "l2": "flushed between steps (256 MiB write outside the timed events); the "
+                         "batch's device state (several GB) is larger than L2",
+                   "parallelism": f"independent batches x{world}" if world > 1 else "1 GPU"},
+        "batched": {"flips_per_s": value, "committed_per_step": com_step,
+                    "generated_per_step": generated,
+                    "wasted_ratio": (generated - com_step) / max(1, com_step),
+                    "iters_mean": iters, "relax_launches_per_step": relax_n // max(1, args.steps),
+                    "relax_ms_per_step": relax_ms / max(1, args.steps)},
+        "one_by_one": one,
+        "batched_over_one_by_one": value / one["flips_per_s"],
+        "plain_L1024": plain_1024,
+        "plain_L8192": plain_8192,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": INT_PEAK_OPS / 1e12,
+                     "unit": "Tops/s", "frac": achieved / INT_PEAK_OPS, "traffic": traffic,
+                     "traffic_unit": "bytes per launch (DRAM read + write; ncu, mean over the "
+                                     "launches of one step)",
                      "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz integer issue",
-                     "kernel": "relax_kernel", "kernel_ms_avg": kms,
+                     "kernel": "relax_kernel<0,2>", "kernel_ms_avg": per_launch_ms,
+                     "committed_per_launch": ev_per_launch,
                      "ops_per_committed_event": OPS_PER_EVENT,
-                     "events_per_s_bounds": {"integer_issue": peak / OPS_PER_EVENT,
-                                             "history_bytes_at_hbm": hbm_bound_events}},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": L * L * len(WINDOWS),
-                "d2h_bytes_per_step": (L * L + 64) * len(WINDOWS)},
-        "gpu_launches": launches,
-        "cpu_baseline": {"value": cpu_committed / cpu_dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "one oracle run of the full workload to t=100 (window "
-                                   "length 1); committed flips over its run time"},
+                     "events_per_s": ev_rate,
+                     "events_per_s_bounds": bounds,
+                     "frac_of_fp64_bound": ev_rate / bounds["fp64_pipe"],
+                     "hbm_peak_gbs": hbm,
+                     "hbm_peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                "h2d_bytes_per_step": int(offs[-1]),
+                "d2h_bytes_per_step": int(offs[-1]) + n * ctypes.sizeof(sr._Obs)},
+        "gpu_launches": int(launches),
+        "cpu_baseline": {"value": cpu_com / cpu_wall, "unit": UNIT, "cores": cores,
+                         "kind": "oracle", "per_core": cpu_per_core,
+                         "sample": f"{len(jobs)} lattices of the batch (3 per side L: coldest, "
+                                   "median, hottest), each from t=0 until about 3e6 committed "
+                                   "events at its rate in the GPU run (at most t=100), one oracle "
+                                   "process per core; committed flips over the wall time"},
         "clocks": _clock_summary(clock_path, local),
-        "batched": batch_info,
         "fg_vs_log_N": fg_rows,
         "wall_s_timed": wall,
     }
@@ -450,17 +581,18 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- profiling and reports
 def run_profile_case(args):
-    """A short slice of the workload for profilers: the L=1024 lattice from
-    t = 0 through `--windows` windows of length `--tw` (one persistent launch)."""
+    """A short slice of the plain workload for profilers: the L=1024 lattice
+    from t = 0 through `--windows` windows of length `--tw` (one persistent
+    launch)."""
     import torch
 
     import paper_cs_0405053_gb300 as sr
     torch.cuda.set_device(0)
-    lat = sr.Lattice(L, J, H_FIELD, TEMP, (RW, RH), seed=1, lanes_per_region=args.lpr,
+    lat = sr.Lattice(PLAIN_L, 1.0, PLAIN_W, PLAIN_H, (16, 16), seed=1, lanes_per_region=args.lpr,
                      lanes_per_warp=args.lpw, time_arith=args.arith, replay_records=args.replay,
                      schedule=args.schedule)
-    t0 = None
     for _ in range(args.warmup):
         lat.reset()
         lat.run_windows(args.tw, args.windows)
@@ -485,28 +617,37 @@ def run_profile_case(args):
 
 
 def run_profile_batch(args):
-    """A short slice of the batched workload for profilers: the 256 lattices
-    in 32x16 regions (32 region lanes per warp, 16 events per window target),
-    one chunk [0, 1) untimed, then `--windows` chunks of one time unit, each
-    chunk one persistent launch."""
+    """The batched workload for profilers, in a fixed configuration (region
+    shape --region, --lpw lanes per warp, --kappa): one untimed step from t = 0
+    to t = 1, then `--windows` more time units (one launch per time unit), or
+    with --windows 0 one whole step (reset, t = 0 to 100)."""
     import torch
 
     import paper_cs_0405053_gb300 as sr
     from paper_cs_0405053_gb300 import workloads
     torch.cuda.set_device(0)
     reps = workloads.batch_replicas()
-    bt = sr.Batch(reps, region=(32, 16), lanes_per_warp=32, schedule=args.schedule)
-    bt.run_adaptive(1.0, kappa=16.0, chunk=1.0)
+    region = tuple(int(v) for v in args.region.split("x"))
+    bt = sr.Batch(reps, region=region, lanes_per_warp=args.lpw, schedule=args.schedule)
+    bt.run_adaptive(1.0, kappa=args.kappa)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    bt.run_adaptive(1.0 + args.windows, kappa=16.0, chunk=1.0)
+    if args.windows > 0:
+        bt.run_adaptive(1.0 + args.windows, kappa=args.kappa)
+    else:
+        bt.reset()
+        bt.run_adaptive(T_END, kappa=args.kappa)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     obs = [bt.observables(b) for b in range(len(reps))]
     com = sum(o.committed for o in obs)
+    gen = sum(o.generated for o in obs)
     print(json.dumps({"profile_batch": True, "chunks": args.windows, "s": dt,
-                      "committed_total": com, "launches": obs[0].launches,
-                      "blocks": bt.blocks, "region_slots_per_block": bt.threads_per_block}))
+                      "committed_total": com, "generated_total": gen,
+                      "flips_per_s": com / dt, "launches": obs[0].launches,
+                      "relax_launches": obs[0].relax_launches, "relax_ms": obs[0].relax_ms,
+                      "blocks": bt.blocks, "region_slots_per_block": bt.threads_per_block,
+                      "region": list(region), "lanes_per_warp": args.lpw, "kappa": args.kappa}))
     return 0
 
 
@@ -546,17 +687,34 @@ def run_scale(args):
     return 0
 
 
+def fluctuation_check(beta, L, ms, fd):
+    """The fluctuation relation d<m>/dh = beta N Var(m), N = L^2, in
+    equilibrium: Var(m) of the instantaneous m over independent replicas at
+    each sample time, averaged over the times (ms [R, times]); its standard
+    error by the jackknife over replicas; against the finite differences fd
+    [R] of the time-averaged m.  Returns the comparison as a dict."""
+    import numpy as np
+    R = ms.shape[0]
+    var = float(ms.var(axis=0, ddof=1).mean())
+    jack = np.array([np.delete(ms, i, axis=0).var(axis=0, ddof=1).mean() for i in range(R)])
+    se_var = math.sqrt((R - 1) / R * float(((jack - jack.mean()) ** 2).sum()))
+    rel, se_rel = beta * L * L * var, beta * L * L * se_var
+    fd_mean, fd_se = float(fd.mean()), float(fd.std(ddof=1) / math.sqrt(R))
+    return {"beta_N_var_m": rel, "beta_N_var_m_se": se_rel, "fd_dm_dh": fd_mean, "fd_se": fd_se,
+            "ratio": rel / fd_mean if fd_mean else None,
+            "z": (fd_mean - rel) / math.hypot(fd_se, se_rel) if (fd_se or se_rel) else None}
+
+
 def run_grad(args):
     """Gradients of time-averaged m and energy per site with respect to
     (beta, h, J) by the score function (autograd backward through the
     library's kernel), against common-random-number central differences
-    (Delta = 1e-3) and, where the chain is in equilibrium, the fluctuation
-    relation dm/dh = beta N Var(m).  Scale "full": 128 replicas of L = 512,
-    t in [50, 200]; "small": 64 replicas of L = 128, t in [10, 40]."""
+    (Delta = 1e-3) and, where the chain is in equilibrium above Tc, the
+    fluctuation relation dm/dh = beta N Var(m).  Scale "full": 128 replicas
+    of L = 512, t in [50, 200]; "small": 64 replicas of L = 128, t in [10, 40]."""
     import numpy as np
     import torch
 
-    import paper_cs_0405053_gb300 as sr
     from paper_cs_0405053_gb300 import grad
     torch.cuda.set_device(0)
     full = args.grad == "full"
@@ -572,6 +730,7 @@ def run_grad(args):
         A = grad.time_averages(theta, spec)
         fwd_s = time.perf_counter() - w0
         row = {"T": T, "h": h, "init": spec.init, "forward_s": round(fwd_s, 3)}
+        fd_dmdh = None
         for j, name in enumerate(("m", "e")):
             theta.grad = None
             A[:, j].sum().backward(retain_graph=True)
@@ -585,20 +744,22 @@ def run_grad(args):
                 ap = grad._simulate(tp.cpu().numpy(), spec)[0][:, j]
                 am = grad._simulate(tm.cpu().numpy(), spec)[0][:, j]
                 fd = (ap - am) / 2e-3
+                if (j, q) == (0, 1):
+                    fd_dmdh = fd
                 fds.append(float(fd.mean()))
                 fdse.append(float(fd.std(ddof=1) / math.sqrt(R)))
             row[f"d{name}"] = {
                 "score": [float(v) for v in est], "score_se": [float(v) for v in se],
                 "fd": fds, "fd_se": fdse,
                 "z": [float((est[q] - fds[q]) / math.hypot(se[q], fdse[q])) for q in range(3)]}
-        if T != 2.269:          # equilibrium: the fluctuation relation of the magnetisation
+        if T > 2.269:          # equilibrium above Tc: the fluctuation relation of m
             _, _, _, ms = grad._simulate(theta.detach().cpu().numpy(), spec, samples=30)
-            # variance over independent replicas at each sample time, averaged
-            row["beta_N_var_m"] = float(beta * Ls * Ls * ms.var(axis=0, ddof=1).mean())
+            row["fluctuation"] = fluctuation_check(beta, Ls, ms, fd_dmdh)
         out.append(row)
+    zs = [abs(z) for r in out for k in ("dm", "de") for z in r[k]["z"]]
     print(json.dumps({"grad": args.grad, "replicas": R, "L": Ls, "t": [t1, t2],
                       "params": "theta = (beta, h, J); d/d theta of the time averages of m and "
-                                "energy per site", "rows": out}), flush=True)
+                                "energy per site", "max_abs_z": max(zs), "rows": out}), flush=True)
     return 0
 
 
@@ -609,7 +770,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-case", action="store_true",
-                    help="run only a short slice of the workload (for ncu)")
+                    help="run only a short slice of the plain workload (for ncu)")
     ap.add_argument("--tw", type=float, default=1.0)
     ap.add_argument("--windows", type=int, default=5)
     ap.add_argument("--lpr", type=int, default=0,
@@ -618,13 +779,12 @@ def main():
     ap.add_argument("--arith", type=int, default=0, help="time arithmetic: 1 FP64, 2 integer")
     ap.add_argument("--schedule", type=int, default=0,
                     help="profile cases: 0 automatic, 1 static, 2 dynamic, 3 asynchronous")
-    ap.add_argument("--batch-t", type=float, default=100.0,
-                    help="simulated time of the batched section")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
+    ap.add_argument("--region", default="32x16", help="profile-batch: region shape WxH")
+    ap.add_argument("--kappa", type=float, default=8.0, help="profile-batch: events per window")
     ap.add_argument("--replay", type=int, default=0,
                     help="checkpoint records per region for incremental replay (0 auto, -1 off)")
     ap.add_argument("--profile-batch", action="store_true",
-                    help="run only a short slice of the batched workload (for ncu)")
+                    help="run only a slice of the batched workload (for ncu)")
     ap.add_argument("--grad", choices=["small", "full"], default=None,
                     help="gradient check of the score-function backward (separate report)")
     ap.add_argument("--scale", action="store_true",

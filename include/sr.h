@@ -144,6 +144,9 @@ typedef struct sr_obs {
   uint64_t run_cycles;          /* SM cycles region slots spent on their regions, summed */
   uint64_t run_cycles_max;      /* the same for the busiest slot */
   uint64_t slots;               /* region slots (lanes or warps) that reported */
+  double relax_ms;              /* device time of this context's relaxation launches since
+                                   creation (CUDA events around each launch on its stream) */
+  uint64_t relax_launches;      /* relaxation launches timed in relax_ms */
 } sr_obs;
 
 /* Create a context with Metropolis rates, fair-coin initial spins and
@@ -298,6 +301,13 @@ int sr_observables_replica(sr_ctx* ctx, int replica, sr_obs* out);
 
 /* Committed spins of lattice `replica` into a host buffer of n = L_b^2 int8. */
 int sr_get_spins_replica(sr_ctx* ctx, int replica, int8_t* host_out, size_t n);
+
+/* Restart lattice `replica` alone from a given configuration (host buffer of
+ * n = L_b^2 int8, > 0 = up, caller-owned; pinned memory makes the copy a
+ * plain DMA): its t_c = 0, every region's clock restarts as at creation
+ * (§5 "First iteration, first step"), its counters are cleared; the other
+ * lattices are untouched.  Blocks.  Errors: SR_EINVAL, SR_ECUDA. */
+int sr_set_spins_replica(sr_ctx* ctx, int replica, const int8_t* host_in, size_t n);
 
 /* Clock state of lattice `replica` as sr_get_carry, n = its region count. */
 int sr_get_carry_replica(sr_ctx* ctx, int replica, uint64_t* index, double* x, double* b,

@@ -82,7 +82,8 @@ class _Obs(C.Structure):
                 ("max_iters_seen", C.c_uint32), ("max_f", C.c_uint32), ("capacity", C.c_uint32),
                 ("launches", C.c_uint64), ("region_passes", C.c_uint64),
                 ("region_skips", C.c_uint64), ("run_cycles", C.c_uint64),
-                ("run_cycles_max", C.c_uint64), ("slots", C.c_uint64)]
+                ("run_cycles_max", C.c_uint64), ("slots", C.c_uint64),
+                ("relax_ms", C.c_double), ("relax_launches", C.c_uint64)]
 
 
 @dataclass
@@ -110,6 +111,8 @@ class Observables:
     run_cycles: int
     run_cycles_max: int
     slots: int
+    relax_ms: float
+    relax_launches: int
 
 
 _lib = None
@@ -151,6 +154,7 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_run_batch": (C.c_int, [_P, _P, _P]),
             "sr_observables_replica": (C.c_int, [_P, C.c_int, C.POINTER(_Obs)]),
             "sr_get_spins_replica": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
+            "sr_set_spins_replica": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
             "sr_get_carry_replica": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_size_t]),
             "sr_run_batch_adaptive": (C.c_int, [_P, _P, C.POINTER(_Adapt), _P]),
             "sr_score": (C.c_int, [_P, _P]),
@@ -532,6 +536,25 @@ class Batch:
         _check(library().sr_get_spins_replica(self._ctx, b, _ptr(out), out.size),
                "sr_get_spins_replica")
         return out
+
+    def spins_into(self, b: int, host_ptr: int) -> None:
+        """Committed spins of lattice b into a caller-owned host buffer of L_b^2 int8."""
+        L = self.replicas[b].L
+        _check(library().sr_get_spins_replica(self._ctx, b, host_ptr, L * L),
+               "sr_get_spins_replica")
+
+    def set_spins(self, b: int, spins) -> None:
+        """Restart lattice b alone from the given spins (t_c = 0)."""
+        L = self.replicas[b].L
+        if isinstance(spins, int):          # a host pointer (e.g. pinned memory)
+            ptr = spins
+        else:
+            a = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
+            if a.size != L * L:
+                raise ValueError(f"lattice {b} has {L * L} sites, got {a.size}")
+            ptr = _ptr(a)
+        _check(library().sr_set_spins_replica(self._ctx, b, ptr, L * L), "sr_set_spins_replica")
+        self.t_c[b] = 0.0
 
     def score(self) -> np.ndarray:
         """[n, 3]: d log L / d(beta, h, J) of every lattice's committed path."""

@@ -85,6 +85,11 @@ struct sr_ctx {
   size_t smem;
   int last_nwin;
   unsigned long long launches;   // kernels launched by this context
+  // device time of the relaxation launches, from events recorded around each
+  // launch on the context's stream
+  cudaEvent_t ev_relax[2];
+  double relax_ms;
+  unsigned long long relax_launches;
 };
 
 namespace {
@@ -354,6 +359,7 @@ int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
   }
   void* args[] = {&k};
   const void* fn = relax_fn(c->mode, c->dynamic);
+  if (c->ev_relax[0] && cudaEventRecord(c->ev_relax[0], c->stream) != cudaSuccess) return SR_ECUDA;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->blocks), dim3(c->tpb), args, c->smem,
                                               c->stream);
   if (e != cudaSuccess) {
@@ -361,12 +367,20 @@ int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
     return SR_ECUDA;
   }
   c->launches += 1;
+  if (c->ev_relax[1] && cudaEventRecord(c->ev_relax[1], c->stream) != cudaSuccess) return SR_ECUDA;
   if (cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream) !=
           cudaSuccess ||
       cudaMemcpyAsync(c->h_rs, c->rs, (size_t)c->nrep * sizeof(RepStats), cudaMemcpyDeviceToHost,
                       c->stream) != cudaSuccess)
     return SR_ECUDA;
-  return cuda_rc(cudaStreamSynchronize(c->stream));
+  rc = cuda_rc(cudaStreamSynchronize(c->stream));
+  if (rc == SR_OK && c->ev_relax[0]) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->ev_relax[0], c->ev_relax[1]) != cudaSuccess) return SR_ECUDA;
+    c->relax_ms += (double)ms;
+    c->relax_launches += 1;
+  }
+  return rc;
 }
 
 // Ring length for windows of length Tw: at most sites * Tw events are expected
@@ -410,6 +424,8 @@ void free_all(sr_ctx* c) {
   if (c->h_obs_i) cudaFreeHost(c->h_obs_i);
   if (c->h_obs_f) cudaFreeHost(c->h_obs_f);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  for (cudaEvent_t ev : c->ev_relax)
+    if (ev) cudaEventDestroy(ev);
   std::free(c->reps);
   std::free(c->hdesc);
   std::free(c->t_c);
@@ -508,6 +524,12 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
       return SR_ECUDA;
     }
     c->own_stream = true;
+  }
+  if (cudaEventCreate(&c->ev_relax[0]) != cudaSuccess ||
+      cudaEventCreate(&c->ev_relax[1]) != cudaSuccess) {
+    free_all(c);
+    std::free(c);
+    return SR_ECUDA;
   }
 
   // launch shape: one warp per region on request; otherwise one lane per
@@ -781,6 +803,8 @@ int observables_of(sr_ctx* c, int b, sr_obs* out) {
   out->max_f = rs.max_f;
   out->capacity = (uint32_t)c->cap;
   out->launches = c->launches;
+  out->relax_ms = c->relax_ms;
+  out->relax_launches = c->relax_launches;
   out->region_passes = h.region_passes;
   out->region_skips = h.region_skips;
   out->run_cycles = h.run_cycles;
@@ -1150,6 +1174,17 @@ int sr_set_spins(sr_ctx* c, const int8_t* host_in, size_t n) {
   if (cudaMemcpyAsync(c->stage, host_in, n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     return SR_ECUDA;
   int rc = init_state(c, 0, c->stage);
+  if (rc) return rc;
+  return cuda_rc(cudaStreamSynchronize(c->stream));
+}
+
+int sr_set_spins_replica(sr_ctx* c, int replica, const int8_t* host_in, size_t n) {
+  if (!c || replica < 0 || replica >= c->nrep || !host_in ||
+      n != (size_t)c->hdesc[replica].L * c->hdesc[replica].L)
+    return SR_EINVAL;
+  if (cudaMemcpyAsync(c->stage, host_in, n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return SR_ECUDA;
+  int rc = init_state(c, replica, c->stage);
   if (rc) return rc;
   return cuda_rc(cudaStreamSynchronize(c->stream));
 }

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle_pool
 
 pytestmark = pytest.mark.gpu
 
@@ -218,6 +219,45 @@ def test_batched_workload_sample_bit_exact():
         assert np.all(batch.t_c == 0.25)
         for b in range(0, len(reps), 11):
             _check_at(batch, b, 16, 16, 0.25)
+
+
+def test_benched_batch_configuration_against_the_oracle():
+    """The batched workload exactly as the benchmark runs it: the autotuner's
+    region shape, lanes per warp and kappa, the automatic (asynchronous)
+    schedule, adaptive window lengths, a warm-up run and a reset, then every
+    lattice to t = 10.  A stratified sample of 15 lattices (the coldest, the
+    median and the hottest of each side L) against their oracle runs: spins,
+    clock carry, counts and observables."""
+    from paper_cs_0405053_gb300 import workloads
+    reps = workloads.batch_replicas()
+    sample = workloads.stratified(reps, per_side=3)
+    assert len(sample) == 15
+    tune = sr.autotune(reps, t_trial=1.0)
+    W, H = tune.region
+    pool = oracle_pool.pool(len(sample))
+    try:
+        jobs = {b: pool.apply_async(oracle_pool.run, (dict(
+            L=reps[b]["L"], J=reps[b]["J"], h=reps[b]["h"], T=reps[b]["T"], region_w=W,
+            region_h=H, seed=reps[b]["seed"], t_end=[10.0]),)) for b in sample}
+        with sr.Batch(reps, region=tune.region, lanes_per_warp=tune.lanes_per_warp) as bt:
+            bt.run_adaptive(1.0, kappa=tune.kappa)
+            bt.reset()
+            bt.run_adaptive(10.0, kappa=tune.kappa)
+            assert np.all(bt.t_c == 10.0)
+            for b in sample:
+                ref = jobs[b].get(timeout=1800)
+                assert np.array_equal(oracle_pool.pack(bt.spins(b)), ref["spins"][0]), b
+                for got, want in zip(bt.carry(b), ref["carry"]):
+                    assert np.array_equal(got, want), b
+                o = bt.observables(b)
+                assert o.committed == int(ref["counts"][0].sum())
+                assert (o.mag, o.bonds) == (int(ref["mag"][0]), int(ref["bonds"][0]))
+                n = reps[b]["L"] ** 2
+                assert abs(o.int_mag - ref["int_mag"][0]) <= 1e-9 * n * 10.0
+                assert abs(o.int_bonds - ref["int_bonds"][0]) <= 1e-9 * n * 10.0
+    finally:
+        pool.terminate()
+        pool.join()
 
 
 # ----------------------------------------------------------------- errors in a batch

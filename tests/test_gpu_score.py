@@ -106,3 +106,57 @@ def test_grad_kernel_matches_its_definition():
     base = (A.sum(axis=0)[None, :] - A) / (n - 1)
     want = np.einsum("ij,ijq->iq", gA, (A - base)[:, :, None] * S[:, None, :] + E)
     assert np.allclose(G.cpu().numpy(), want, rtol=1e-12, atol=1e-12)
+
+
+def _fd(theta, spec, q, j, d=1e-3):
+    tp, tm = theta.detach().clone(), theta.detach().clone()
+    tp[:, q] += d
+    tm[:, q] -= d
+    ap = grad._simulate(tp.cpu().numpy(), spec)[0][:, j]
+    am = grad._simulate(tm.cpu().numpy(), spec)[0][:, j]
+    return (ap - am) / (2 * d)
+
+
+@pytest.mark.parametrize("h", [0.0, 0.05])
+def test_c5_shaped_gradients_at_and_off_the_kink(h):
+    """The differentiation workload's shape at a smaller size: 128 replicas
+    of L = 256 at T = 2.8 from fair-coin spins, time averages of m and the
+    energy per site over t in [40, 100].  All six score-function derivatives
+    (d/d(beta, h, J) of both averages) against common-random-number central
+    differences (Delta = 1e-3) within 3.5 combined standard errors.  At h = 0
+    the n_up = 2 classes sit on the kink of the Metropolis rate (the score
+    takes the mean of the one-sided derivatives there).  At h = 0 also the
+    fluctuation relation d<m>/dh = beta N Var(m) (N = L^2, the variance of the
+    instantaneous m over the independent replicas): the chain is in
+    equilibrium over the averaging interval, so the central difference of the
+    time average must agree with it within 4 standard errors (jackknife over
+    replicas for the variance)."""
+    R, L, T = 128, 256, 2.8
+    beta = 1.0 / T
+    spec = grad.AverageSpec(L=[L] * R, seeds=list(range(9000, 9000 + R)), t1=40.0, t2=100.0)
+    theta = torch.tensor([[beta, h, 1.0]] * R, dtype=torch.float64, device="cuda",
+                         requires_grad=True)
+    A = grad.time_averages(theta, spec)
+    zs = []
+    fd_dmdh = None
+    for j in range(2):
+        theta.grad = None
+        A[:, j].sum().backward(retain_graph=True)
+        g = theta.grad.detach().cpu().numpy()
+        est, se = g.mean(axis=0), g.std(axis=0, ddof=1) / math.sqrt(R)
+        for q in range(3):
+            fd = _fd(theta, spec, q, j)
+            z = (est[q] - fd.mean()) / math.hypot(se[q], fd.std(ddof=1) / math.sqrt(R))
+            zs.append(z)
+            if (j, q) == (0, 1):
+                fd_dmdh = fd
+    assert max(abs(z) for z in zs) <= 3.5, zs
+    if h == 0.0:
+        _, _, _, ms = grad._simulate(theta.detach().cpu().numpy(), spec, samples=30)
+        var = ms.var(axis=0, ddof=1).mean()
+        jack = np.array([np.delete(ms, i, axis=0).var(axis=0, ddof=1).mean() for i in range(R)])
+        se_var = math.sqrt((R - 1) / R * ((jack - jack.mean()) ** 2).sum())
+        rel = beta * L * L * var
+        se_rel = beta * L * L * se_var
+        z = (fd_dmdh.mean() - rel) / math.hypot(fd_dmdh.std(ddof=1) / math.sqrt(R), se_rel)
+        assert abs(z) <= 4.0, (fd_dmdh.mean(), rel, z)
