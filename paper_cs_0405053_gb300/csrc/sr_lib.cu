@@ -1538,9 +1538,9 @@ int noalloc_scratch(void** out) {
   return SR_OK;
 }
 
-// Carve a 256-byte-aligned piece of `bytes` out of the scratch.
+// Carve 256-byte-aligned pieces out of the scratch, starting at address `base`.
 struct Carver {
-  unsigned char* base;
+  uintptr_t base;
   size_t used;
   template <class T>
   T* take(size_t count) {
@@ -1550,6 +1550,44 @@ struct Carver {
     return p;
   }
 };
+
+// The working state of sr_run_noalloc laid out from `base` (the scratch's
+// device address, or 0 to measure the layout without touching the GPU): fills
+// every device pointer of c, in one fixed order, and returns the bytes used.
+// The size check and the real layout both run this one sequence.
+size_t noalloc_layout(sr_ctx& c, uintptr_t base) {
+  const size_t nr = (size_t)c.NR, H = (size_t)c.prm.region_h;
+  Carver cv{base, 0};
+  c.rows = cv.take<uint32_t>(2 * H * nr);
+  c.halo = cv.take<uint32_t>(4 * nr);
+  c.ci = cv.take<unsigned long long>(2 * nr);
+  c.cx = cv.take<double>(2 * nr);
+  c.ckv = cv.take<unsigned long long>(2 * nr);
+  c.cb = cv.take<double>(2 * nr);
+  c.ct = cv.take<double>(2 * nr);
+  c.cim = cv.take<double>(2 * nr);
+  c.cib = cv.take<double>(2 * nr);
+  c.ht = cv.take<double>((size_t)2 * 4 * kNoallocCap * nr);
+  c.hp = cv.take<uint8_t>((size_t)2 * 4 * kNoallocCap * nr);
+  c.hl = cv.take<uint32_t>(2 * 4 * nr);
+  c.chg = cv.take<uint8_t>(2 * nr);
+  c.rx = cv.take<double>((size_t)kNoallocRing * nr);
+  c.rkv = cv.take<unsigned long long>((size_t)kNoallocRing * nr);
+  c.rhi = cv.take<unsigned long long>(nr);
+  c.st = cv.take<DevStats>(1);
+  c.win_iters = cv.take<uint32_t>(2 * (size_t)kWinRing);
+  c.curf = cv.take<uint32_t>(2);
+  c.desc = cv.take<RepDesc>(1);
+  c.rs = cv.take<RepStats>(1);
+  c.rflags = cv.take<uint32_t>(3);
+  c.rrep = cv.take<uint32_t>(nr);
+  c.rn = cv.take<uint32_t>(nr);
+  c.rwin = cv.take<uint32_t>(nr);
+  c.rts = cv.take<double>(nr);
+  c.rcidx = cv.take<uint8_t>(nr);
+  c.rfill = cv.take<uint8_t>(nr);
+  return cv.used;
+}
 
 }  // namespace
 
@@ -1606,29 +1644,9 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.Lmax = L;
   c.stream = (cudaStream_t)stream;
 
-  // size check before touching the GPU
-  const size_t nr = (size_t)c.NR, H = (size_t)region_h;
-  Carver probe{nullptr, 0};
-  probe.take<uint32_t>(2 * H * nr);               // rows
-  probe.take<uint32_t>(4 * nr);                   // halos
-  for (int a = 0; a < 7; ++a) probe.take<double>(2 * nr);   // carry
-  probe.take<double>((size_t)2 * 4 * kNoallocCap * nr);     // list times
-  probe.take<uint8_t>((size_t)2 * 4 * kNoallocCap * nr);    // list positions
-  probe.take<uint32_t>(2 * 4 * nr);               // list lengths
-  probe.take<uint8_t>(2 * nr);                    // list-changed flags
-  probe.take<double>((size_t)kNoallocRing * nr);  // ring x
-  probe.take<unsigned long long>((size_t)kNoallocRing * nr);  // ring V
-  probe.take<unsigned long long>(nr);             // ring ends
-  probe.take<DevStats>(1);
-  probe.take<uint32_t>(2 * (size_t)kWinRing);
-  probe.take<uint32_t>(2);                        // f of the running window
-  probe.take<RepDesc>(1);                         // lattice descriptor and counters
-  probe.take<RepStats>(1);
-  probe.take<uint32_t>(3);                        // convergence flags
-  probe.take<uint32_t>(3 * nr);                   // lattice, iteration, window of each region
-  probe.take<double>(nr);                         // window start of each region
-  probe.take<uint8_t>(2 * nr);                    // committed copy, ring top-up pending
-  if (probe.used > (size_t)SR_NOALLOC_SCRATCH_BYTES) return SR_ETOOLARGE;
+  // size check before touching the GPU: the same layout, measured from 0
+  const size_t nr = (size_t)c.NR;
+  if (noalloc_layout(c, 0) > (size_t)SR_NOALLOC_SCRATCH_BYTES) return SR_ETOOLARGE;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1638,35 +1656,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   void* base = nullptr;
   int rc = noalloc_scratch(&base);
   if (rc != SR_OK) return rc;
-  Carver cv{(unsigned char*)base, 0};
-  c.rows = cv.take<uint32_t>(2 * H * nr);
-  c.halo = cv.take<uint32_t>(4 * nr);
-  c.ci = cv.take<unsigned long long>(2 * nr);
-  c.cx = cv.take<double>(2 * nr);
-  c.ckv = cv.take<unsigned long long>(2 * nr);
-  c.cb = cv.take<double>(2 * nr);
-  c.ct = cv.take<double>(2 * nr);
-  c.cim = cv.take<double>(2 * nr);
-  c.cib = cv.take<double>(2 * nr);
-  c.ht = cv.take<double>((size_t)2 * 4 * kNoallocCap * nr);
-  c.hp = cv.take<uint8_t>((size_t)2 * 4 * kNoallocCap * nr);
-  c.hl = cv.take<uint32_t>(2 * 4 * nr);
-  c.chg = cv.take<uint8_t>(2 * nr);
-  c.rx = cv.take<double>((size_t)kNoallocRing * nr);
-  c.rkv = cv.take<unsigned long long>((size_t)kNoallocRing * nr);
-  c.rhi = cv.take<unsigned long long>(nr);
-  c.st = cv.take<DevStats>(1);
-  c.win_iters = cv.take<uint32_t>(2 * (size_t)kWinRing);
-  c.curf = cv.take<uint32_t>(2);
-  c.desc = cv.take<RepDesc>(1);
-  c.rs = cv.take<RepStats>(1);
-  c.rflags = cv.take<uint32_t>(3);
-  c.rrep = cv.take<uint32_t>(nr);
-  c.rn = cv.take<uint32_t>(nr);
-  c.rwin = cv.take<uint32_t>(nr);
-  c.rts = cv.take<double>(nr);
-  c.rcidx = cv.take<uint8_t>(nr);
-  c.rfill = cv.take<uint8_t>(nr);
+  if (noalloc_layout(c, (uintptr_t)base) > (size_t)SR_NOALLOC_SCRATCH_BYTES) return SR_ETOOLARGE;
   c.cap = kNoallocCap;
   c.K = kNoallocRing;
   c.Kcap = kNoallocRing;

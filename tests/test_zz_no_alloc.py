@@ -52,6 +52,7 @@ def test_no_alloc_equals_the_allocating_entry_points_on_two_calls():
     cases = [
         (64, 16, 16, 1.0, 0.05, 1.5, 1, 1.0, 5, None),      # fair coin from the seed
         (96, 8, 12, 1.0, 0.0, 2.3, 7, 0.5, 6, given),       # caller-given spins
+        (32, 8, 8, 1.0, 0.1, float("inf"), 3, 0.25, 4, None),   # T = inf: every p_k = 1
     ]
     for case in cases:          # two calls in a row share the same scratch
         a_spins, a_counts = _run_noalloc(*case)
