@@ -48,28 +48,65 @@ __device__ void fill_ring(const KParams& p) {
   __syncthreads();
 }
 
-// Ring top-up of one region by one lane (asynchronous schedule): the pairs of
-// events [max(rhi, i_c), i_c + K) (all K under the alternate step rule, whose
-// window wg starts on new numbers).
-__device__ void fill_own(const KParams& p, int r, const Lat& lt, unsigned wg) {
+// Ring top-up of the regions of a commit task by the whole warp (asynchronous
+// schedule).  The region r of a lane with `want` needs the pairs of events
+// [max(rhi, i_c), i_c + K) (all K under the alternate step rule, whose window
+// wg starts on new numbers); the warp draws the pairs of all its regions 32 at
+// a time, so a region's top-up is not a serial chain of draws on its lattice's
+// path.  Every lane of the warp calls it.
+template <bool GEN>
+__device__ void fill_warp(const KParams& p, bool want, int r, uint32_t loc, uint32_t key0,
+                          uint32_t key1, unsigned wg) {
+  constexpr unsigned kAll = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
   const size_t nr = (size_t)p.NR;
   const unsigned long long kmask = (unsigned long long)p.K - 1ull;
-  const unsigned long long lo = __ldcg(&p.ci[(size_t)p.rcidx[r] * nr + r]);
-  const unsigned long long hi_old = p.rhi[r];
-  const unsigned long long from = (hi_old > lo && !p.fresh) ? hi_old : lo;
-  const unsigned long long to = lo + (unsigned long long)p.K;
-  for (unsigned long long i = from; i < to; ++i) {
-    double x;
-    unsigned long long kv;
-    if (p.fresh)
-      draw_event_fresh((unsigned)(i - lo), wg, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
-    else
-      draw_event(i, (uint32_t)lt.loc, lt.key0, lt.key1, x, kv);
-    const size_t a = (size_t)(i & kmask) * nr + r;
-    p.rx[a] = x;
-    p.rkv[a] = kv;
+  const bool fresh = GEN && p.fresh;
+  unsigned long long lo = 0ull, from = 0ull, to = 0ull;
+  if (want) {
+    lo = __ldcg(&p.ci[(size_t)p.rcidx[r] * nr + r]);
+    const unsigned long long hi_old = p.rhi[r];
+    from = (hi_old > lo && !fresh) ? hi_old : lo;
+    to = lo + (unsigned long long)p.K;
   }
-  p.rhi[r] = to;
+  const unsigned cnt = want ? (unsigned)(to - from) : 0u;     // at most K <= 4096
+  unsigned incl = cnt;                                        // inclusive prefix over lanes
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned o = __shfl_up_sync(kAll, incl, d);
+    if (lane >= d) incl += o;
+  }
+  const unsigned total = __shfl_sync(kAll, incl, 31);
+  for (unsigned k0 = 0; k0 < total; k0 += 32) {
+    const unsigned k = k0 + (unsigned)lane;
+    // the lane whose range holds draw k: the number of lanes with prefix <= k
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const unsigned v = __shfl_sync(kAll, incl, owner + step - 1);
+      if (v <= k) owner += step;
+    }
+    owner &= 31;                                              // k >= total: no draw
+    const unsigned excl = __shfl_sync(kAll, incl - cnt, owner);
+    const unsigned long long ofrom = __shfl_sync(kAll, from, owner);
+    const unsigned long long olo = __shfl_sync(kAll, lo, owner);
+    const int orr = __shfl_sync(kAll, r, owner);
+    const uint32_t oloc = __shfl_sync(kAll, loc, owner);
+    const uint32_t ok0 = __shfl_sync(kAll, key0, owner), ok1 = __shfl_sync(kAll, key1, owner);
+    if (k < total) {
+      const unsigned long long i = ofrom + (unsigned long long)(k - excl);
+      double x;
+      unsigned long long kv;
+      if (fresh)
+        draw_event_fresh((unsigned)(i - olo), wg, oloc, ok0, ok1, x, kv);
+      else
+        draw_event(i, oloc, ok0, ok1, x, kv);
+      const size_t a = (size_t)(i & kmask) * nr + (size_t)orr;
+      p.rx[a] = x;
+      p.rkv[a] = kv;
+    }
+  }
+  if (want) p.rhi[r] = to;
 }
 
 // Task queue of the asynchronous schedule: a task is (kind, lattice, chunk of
@@ -100,8 +137,10 @@ __device__ void enqueue_lattice(const KParams& p, int b, unsigned kind, int chun
 // MODE 0 / 2: one lane per region with FP64 / integer-emulated time
 // arithmetic; the first `lanes` lanes of every warp are region lanes.  MODE 1:
 // one warp per region.  Region slot j of block b owns regions
-// b*rl + j + k*(gridDim.x*rl).
-template <int MODE, int DYN>
+// b*rl + j + k*(gridDim.x*rl).  GEN = false: no score mode, alternate step
+// rule or trace (see run_region); with the asynchronous schedule the rings
+// are then filled for the whole launch at its start and commits draw nothing.
+template <int MODE, int DYN, bool GEN>
 __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
                                    MODE == 1 ? SR_WARP_MIN_BLOCKS : SR_LANE_MIN_BLOCKS)
     relax_kernel(KParams p) {
@@ -241,10 +280,10 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
                                         __ldcg(&p.ci[(size_t)(cnew ^ 1u) * nr + r]);
           if (dc) atomicAdd(&rs->committed, dc);
           p.rcidx[r] = (uint8_t)cnew;
-          const Lat lt = lat_of(p, r);
-          compute_halo(p, lt, r, cnew);
-          if (w + 1u < (unsigned)d->nwin) fill_own(p, r, lt, d->w0 + w + 1u);
+          compute_halo(p, lat_of(p, r), r, cnew);
         }
+        fill_warp<GEN>(p, mine && w + 1u < (unsigned)d->nwin, r, (uint32_t)loc, d->key0, d->key1,
+                       d->w0 + w + 1u);
         __syncwarp();        // every lane's writes come before lane 0's release
         if (lane == 0) {
           __threadfence();
@@ -289,9 +328,9 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
           const Lat lt = lat_of(p, r);
           const unsigned cidx = p.rcidx[r];
           if (MODE == 2)
-            run_region<1>(p, lt, r, (int)n, cidx, t_s, t_end, d->w0 + w, g, ra);
+            run_region<1, GEN>(p, lt, r, (int)n, cidx, t_s, t_end, d->w0 + w, g, ra);
           else
-            run_region<0>(p, lt, r, (int)n, cidx, t_s, t_end, d->w0 + w, g, ra);
+            run_region<0, GEN>(p, lt, r, (int)n, cidx, t_s, t_end, d->w0 + w, g, ra);
           if (ra.fmax) atomicMax(&p.curf[(w & 1u) * p.nrep + b], ra.fmax);
           if (ra.events) atomicAdd(&rs->generated, (unsigned long long)ra.events);
           if (ra.breaks) atomicAdd(&rs->breaks, (unsigned long long)ra.breaks);
@@ -381,9 +420,9 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
       Acc ra = {0u, 0u, 0u, 0u, 0u, 0u, false, false};
       const unsigned wg = d->w0 + p.rwin[r];
       if (MODE == 0)
-        run_region<0>(p, lt, r, n, cidx, t_s, t_end, wg, g, ra);
+        run_region<0, GEN>(p, lt, r, n, cidx, t_s, t_end, wg, g, ra);
       else if (MODE == 2)
-        run_region<1>(p, lt, r, n, cidx, t_s, t_end, wg, g, ra);
+        run_region<1, GEN>(p, lt, r, n, cidx, t_s, t_end, wg, g, ra);
       else
         run_region_warp(p, lt, r, n, cidx, t_s, t_end, ra);
       if (reporter) {

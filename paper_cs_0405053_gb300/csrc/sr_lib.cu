@@ -233,16 +233,26 @@ int alloc_history(sr_ctx* c, int cap) {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SR_OK : SR_ECUDA; }
 
-// The kernel instance of a mapping (0 lane/FP64, 1 warp, 2 lane/integer time)
-// and schedule (static or dynamic).
-const void* relax_fn(int mode, int dynamic) {
+// The kernel instance of a mapping (0 lane/FP64, 1 warp, 2 lane/integer time),
+// schedule (static, dynamic, asynchronous) and feature set (gen: score mode,
+// the alternate step rule or a trace; the lean instances carry none of them).
+const void* relax_fn(int mode, int dynamic, bool gen) {
+  if (mode == 1)
+    return dynamic ? (const void*)relax_kernel<1, 1, true> : (const void*)relax_kernel<1, 0, true>;
+  if (mode == 2) {
+    if (dynamic == 2) return (const void*)relax_kernel<2, 2, true>;
+    return dynamic ? (const void*)relax_kernel<2, 1, true> : (const void*)relax_kernel<2, 0, true>;
+  }
   if (dynamic == 2)
-    return mode == 2 ? (const void*)relax_kernel<2, 2> : (const void*)relax_kernel<0, 2>;
+    return gen ? (const void*)relax_kernel<0, 2, true> : (const void*)relax_kernel<0, 2, false>;
   if (dynamic)
-    return mode == 1 ? (const void*)relax_kernel<1, 1>
-                     : (mode == 2 ? (const void*)relax_kernel<2, 1> : (const void*)relax_kernel<0, 1>);
-  return mode == 1 ? (const void*)relax_kernel<1, 0>
-                   : (mode == 2 ? (const void*)relax_kernel<2, 0> : (const void*)relax_kernel<0, 0>);
+    return gen ? (const void*)relax_kernel<0, 1, true> : (const void*)relax_kernel<0, 1, false>;
+  return gen ? (const void*)relax_kernel<0, 0, true> : (const void*)relax_kernel<0, 0, false>;
+}
+
+// The context uses score mode, the alternate step rule or a trace.
+bool gen_features(const sr_params& p) {
+  return p.score != 0 || p.fresh_steps != 0 || p.trace_capacity > 0;
 }
 
 // Shared memory of a lane-mapping block: per region slot, H spin rows, ten
@@ -358,7 +368,7 @@ int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
       return SR_ECUDA;
   }
   void* args[] = {&k};
-  const void* fn = relax_fn(c->mode, c->dynamic);
+  const void* fn = relax_fn(c->mode, c->dynamic, gen_features(c->prm));
   if (c->ev_relax[0] && cudaEventRecord(c->ev_relax[0], c->stream) != cudaSuccess) return SR_ECUDA;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(c->blocks), dim3(c->tpb), args, c->smem,
                                               c->stream);
@@ -568,7 +578,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     c->smem = lane_smem_bytes(H, c->rl, p.score != 0);
   }
   {
-    const void* fn = relax_fn(c->mode, 0);
+    const void* fn = relax_fn(c->mode, 0, gen_features(p));
     cudaFuncAttributes fa;
     int per_sm_blocks = 0;
     if (!allow_smem(fn, c->smem) || cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
@@ -596,7 +606,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
                              ? 1 : 0;
     if (c->dynamic) {
       // the dynamic instance: same launch bounds; check it fits the same grid
-      const void* fd = relax_fn(c->mode, c->dynamic);
+      const void* fd = relax_fn(c->mode, c->dynamic, gen_features(p));
       int bd = 0;
       if (!allow_smem(fd, c->smem) ||
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, fd, c->tpb, c->smem) != cudaSuccess ||
@@ -1675,8 +1685,9 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.tpb = tpb;
   c.smem = lane_smem_bytes(region_h, rl, false);
   int per_sm_blocks = 0;
-  if (!allow_smem((const void*)relax_kernel<0, 0>, c.smem) ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0, 0>, tpb, c.smem) !=
+  if (!allow_smem((const void*)relax_kernel<0, 0, false>, c.smem) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blocks, relax_kernel<0, 0, false>, tpb,
+                                                    c.smem) !=
           cudaSuccess ||
       per_sm_blocks < 1) {
     cudaGetLastError();
@@ -1705,7 +1716,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
     return SR_ECUDA;
   KParams k = make_params(&c);
   void* args[] = {&k};
-  if (cudaLaunchCooperativeKernel((const void*)relax_kernel<0, 0>, dim3(c.blocks), dim3(c.tpb), args,
+  if (cudaLaunchCooperativeKernel((const void*)relax_kernel<0, 0, false>, dim3(c.blocks), dim3(c.tpb), args,
                                   c.smem, c.stream) != cudaSuccess) {
     cudaGetLastError();
     return SR_ECUDA;

@@ -19,6 +19,9 @@ struct Acc {
 // parity wp, comparing them with its lists of the previous iteration.
 // SOFT = 1: the waiting-time chain in integer-emulated doubles; 0: FP64
 // instructions.  Both round every operation once (IEEE), so the bits agree.
+// GEN = false compiles out score mode, the alternate step rule and the
+// event trace (a smaller loop body for the common case); GEN = true reads
+// them from the launch parameters.
 template <int SOFT>
 __device__ __forceinline__ double tau_any(double t_last, double x, double b, unsigned long long lam,
                                           const KParams& p) {
@@ -31,10 +34,12 @@ __device__ __forceinline__ double accrue_any(double b, double tb, double tl, uns
               : accrue(b, tb, tl, lam, p.scale);
 }
 
-template <int SOFT>
+template <int SOFT, bool GEN>
 __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, unsigned cidx,
                            double t_s, double t_end, unsigned wg, Region& g, Acc& acc) {
   const int W = p.W, H = p.H, NR = p.NR;
+  const bool score = GEN && p.score, fresh = GEN && p.fresh;
+  const int tcap = GEN ? p.tcap : 0;
   const int wp = n_iter & 1;
   const int rp = wp ^ 1;
   const int rx = lt.loc % lt.NX, ry = lt.loc / lt.NX;
@@ -218,8 +223,8 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     i = p.ci[cidx * nr + r];        // first event of the window
     // the carry of §5 "Subsequent steps", or (alternate rule) a clock that
     // restarts at the window start with no hazard accrued
-    b = p.fresh ? 0.0 : p.cb[cidx * nr + r];
-    tl = p.fresh ? t_s : p.ct[cidx * nr + r];
+    b = fresh ? 0.0 : p.cb[cidx * nr + r];
+    tl = fresh ? t_s : p.ct[cidx * nr + r];
   }
   // presimulated pairs (U, V) of the coming events (§4: the random numbers
   // as a list drawn before use); the pair of event i+1 is loaded one event ahead
@@ -227,13 +232,13 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   const unsigned kmask = (unsigned)p.K - 1u;     // K is a power of two <= 4096
   // events past the ring are drawn here (alternate rule: numbered from the window start)
   auto draw_at = [&](unsigned long long ii, double& xx, unsigned long long& kk) {
-    if (p.fresh)
+    if (fresh)
       draw_event_fresh((unsigned)(ii - p.ci[cidx * nr + r]), wg, (uint32_t)lt.loc, lt.key0,
                        lt.key1, xx, kk);
     else
       draw_event(ii, (uint32_t)lt.loc, lt.key0, lt.key1, xx, kk);
   };
-  if (!resume && !p.fresh) {
+  if (!resume && !fresh) {
     x = p.cx[cidx * nr + r];
     kv = p.ckv[cidx * nr + r];
   } else if (i < hi) {
@@ -320,7 +325,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   // window integrals of the observables in fixed point (times as multiples of 2^-frac)
   const int frac = 62 - (int)((((unsigned long long)__double_as_longlong(t_end)) >> 52) - 1022);
   const long long tend_b = __double_as_longlong(t_end);
-  if (p.score) {
+  if (score) {
     // the window's occupancy sums start at -N_k(t_s) t_s, its event counts at 0
     const unsigned long long tf0 = to_fixed(t_s, frac);
 #pragma unroll
@@ -450,7 +455,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       const int beta = sig * (nup - 2);
       {
         const unsigned long long tfix = to_fixed(tau, frac);
-        if (p.score)                   // score statistics of the event and its class moves
+        if (score)                     // score statistics of the event and its class moves
           score_event(g, cv, s_old, dnb, tfix, vE ? cE : -1, vW ? cW : -1, vS ? cS : -1,
                       vN ? cN : -1);
         ksig += sig;
@@ -493,9 +498,9 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
         }
       }
       if (boundary) ++bevents;
-      if (p.tcap > 0 && i < (unsigned long long)p.tcap) {
-        p.trt[(size_t)r * p.tcap + i] = tau;
-        p.trs[(size_t)r * p.tcap + i] =
+      if (tcap > 0 && i < (unsigned long long)tcap) {
+        p.trt[(size_t)r * tcap + i] = tau;
+        p.trs[(size_t)r * tcap + i] =
             ((uint32_t)(ry * H) + fy) * (uint32_t)lt.L + (uint32_t)(rx * W) + fx;
       }
       ++events;
@@ -533,7 +538,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       lam += g.P(cu_new) - g.P(cu_old);
       N.move(cu_old, cu_new);
       g.c_move(cu_old, cu_new, uy);
-      if (p.score) g.occ_move(cu_old, cu_new, to_fixed(tb, frac));
+      if (score) g.occ_move(cu_old, cu_new, to_fixed(tb, frac));
       // checkpoint after this break point, for the next pass's replay
       if (nrec < (unsigned)p.CB) {
         uint32_t* rec = rec0 + (size_t)nrec * rwords;
@@ -602,7 +607,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     p.cim[tc * nr + r] = __dadd_rn(p.cim[cidx * nr + r], im);
     p.cib[tc * nr + r] = __dadd_rn(p.cib[cidx * nr + r], ib);
   }
-  if (p.score) {
+  if (score) {
     // close the window's occupancy sums with N_k(t_end) t_end; add to the totals
     const unsigned long long tfe = to_fixed(t_end, frac);
     for (int k = 0; k < 10; ++k) {
