@@ -202,16 +202,17 @@ def _oracle_pool(n):
     return mp.get_context("spawn").Pool(n)
 
 
-def oracle_sample(reps, region, rates, events_per_job=3.0e6):
+def oracle_sample(reps, shapes, rates, events_per_job=3.0e6):
     """A bounded sample of the batched workload for the oracle: a stratified
-    set of lattices (every side L, cold to hot), each run from t = 0 to the
-    time at which it has committed about `events_per_job` events at its own
-    event rate `rates[b]` (events per unit time), at most t = 100."""
+    set of lattices (every side L, cold to hot), each in its region shape
+    shapes[b], run from t = 0 to the time at which it has committed about
+    `events_per_job` events at its own event rate `rates[b]` (events per unit
+    time), at most t = 100."""
     from paper_cs_0405053_gb300 import workloads
     jobs = []
     for b in workloads.stratified(reps, per_side=3):
         t_end = min(T_END, max(0.25, events_per_job / max(rates[b], 1.0)))
-        rep = dict(reps[b], W=region[0], H=region[1])
+        rep = dict(reps[b], W=shapes[b][0], H=shapes[b][1])
         jobs.append((rep, float(t_end)))
     return jobs
 
@@ -251,7 +252,7 @@ def run_reference(args):
     pool = _oracle_pool(cores)
     try:
         rates = _calibrated_rates(pool, reps, region)
-        jobs = oracle_sample(reps, region, rates, events_per_job=1.5e6)
+        jobs = oracle_sample(reps, [region] * len(reps), rates, events_per_job=1.5e6)
         for _ in range(args.warmup):
             run_oracle_sample(pool, jobs[:cores])
         committed, secs = 0, 0.0
@@ -353,8 +354,9 @@ def _one_by_one(sr, torch, stream, reps, tune, every=16):
     shape and window rule, run one after the other."""
     com, dev = 0, 0.0
     sample = list(range(0, len(reps), every))
+    own = tune.replicas(reps)
     for k in sample:
-        one = sr.Batch([reps[k]], region=tune.region)
+        one = sr.Batch([own[k]], region=tune.shapes[k])
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         torch.cuda.synchronize()
         ev[0].record(stream)
@@ -417,7 +419,11 @@ def run_ours(args):
     t0 = time.perf_counter()
     tune = sr.autotune(reps, t_trial=1.0)
     tune_s = time.perf_counter() - t0
-    bt = sr.Batch(reps, region=tune.region, lanes_per_warp=tune.lanes_per_warp)
+    bt = sr.Batch(tune.replicas(reps), region=tune.region, lanes_per_warp=tune.lanes_per_warp)
+    if args.tune_out:
+        with open(args.tune_out, "w") as fh:
+            json.dump({"shapes": tune.shapes, "lanes_per_warp": tune.lanes_per_warp,
+                       "kappa": tune.kappa, "rate_threshold": tune.rate_threshold}, fh)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     n = len(reps)
 
@@ -501,7 +507,7 @@ def run_ours(args):
     cores = max(1, min(os.cpu_count() or 1, 16))
     pool = _oracle_pool(cores)
     try:
-        jobs = oracle_sample(reps, tune.region, rates)
+        jobs = oracle_sample(reps, tune.shapes, rates)
         cpu_com, cpu_wall, cpu_per_core = run_oracle_sample(pool, jobs)
     finally:
         pool.terminate()
@@ -515,15 +521,19 @@ def run_ours(args):
     achieved = ev_per_launch * OPS_PER_EVENT / (per_launch_ms * 1e-3)
     peaks = _measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_GBS_FALLBACK))
-    W, H = tune.region
-    phi = (2 * W + 2 * H - 4) / (W * H)                 # boundary sites of a region
+    # boundary sites per site of each lattice's regions, weighted by its committed events
+    phi = sum(o.committed * (2 * w + 2 * h - 4) / (w * h)
+              for o, (w, h) in zip(obs, tune.shapes)) / max(1, com_step)
     ev_rate = committed / (relax_ms * 1e-3)
     bounds = {"integer_issue": INT_PEAK_OPS / OPS_PER_EVENT,
               "history_bytes_at_hbm": hbm * 1e9 / (HIST_BYTES_PER_BOUNDARY_EVENT * phi),
               "fp64_pipe": FP64_PEAK_OPS / FP64_SLOTS_PER_EVENT}
     traffic = None
+    shape_counts = {}
+    for w, h in tune.shapes:
+        shape_counts[f"{w}x{h}"] = shape_counts.get(f"{w}x{h}", 0) + 1
     if (BATCH_TRAFFIC and _kernel_sources_sha() == BATCH_TRAFFIC_SHA and
-            BATCH_TRAFFIC["tuning"] == [W, H, tune.lanes_per_warp, tune.kappa]):
+            BATCH_TRAFFIC["tuning"] == [shape_counts, tune.lanes_per_warp, tune.kappa]):
         traffic = BATCH_TRAFFIC["bytes_per_launch"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -531,7 +541,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded lattices, fair-coin spins)",
         "config": {"workload": WORKLOAD, "lattices": n, "sites": int(offs[-1]),
-                   "tuning": {"region": list(tune.region),
+                   "tuning": {"region_shapes": shape_counts,
+                              "rate_threshold": tune.rate_threshold,
                               "lanes_per_warp": tune.lanes_per_warp or "auto",
                               "kappa": tune.kappa, "trials": tune.trials,
                               "seconds": round(tune_s, 2)},
@@ -628,7 +639,14 @@ def run_profile_batch(args):
     torch.cuda.set_device(0)
     reps = workloads.batch_replicas()
     region = tuple(int(v) for v in args.region.split("x"))
-    bt = sr.Batch(reps, region=region, lanes_per_warp=args.lpw, schedule=args.schedule)
+    lpw, kappa = args.lpw, args.kappa
+    if args.tune_in:
+        with open(args.tune_in) as fh:
+            t = json.load(fh)
+        reps = [dict(r, region=tuple(s)) for r, s in zip(reps, t["shapes"])]
+        lpw, kappa = t["lanes_per_warp"], t["kappa"]
+    args.kappa = kappa
+    bt = sr.Batch(reps, region=region, lanes_per_warp=lpw, schedule=args.schedule)
     bt.run_adaptive(1.0, kappa=args.kappa)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -647,7 +665,8 @@ def run_profile_batch(args):
                       "flips_per_s": com / dt, "launches": obs[0].launches,
                       "relax_launches": obs[0].relax_launches, "relax_ms": obs[0].relax_ms,
                       "blocks": bt.blocks, "region_slots_per_block": bt.threads_per_block,
-                      "region": list(region), "lanes_per_warp": args.lpw, "kappa": args.kappa}))
+                      "region": list(region), "lanes_per_warp": lpw, "kappa": kappa,
+                      "tune_in": args.tune_in}))
     return 0
 
 
@@ -781,6 +800,9 @@ def main():
                     help="profile cases: 0 automatic, 1 static, 2 dynamic, 3 asynchronous")
     ap.add_argument("--region", default="32x16", help="profile-batch: region shape WxH")
     ap.add_argument("--kappa", type=float, default=8.0, help="profile-batch: events per window")
+    ap.add_argument("--tune-out", default=None, help="write the autotuner's choice to this file")
+    ap.add_argument("--tune-in", default=None,
+                    help="profile-batch: region shapes, lanes per warp and kappa from this file")
     ap.add_argument("--replay", type=int, default=0,
                     help="checkpoint records per region for incremental replay (0 auto, -1 off)")
     ap.add_argument("--profile-batch", action="store_true",

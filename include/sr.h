@@ -107,14 +107,18 @@ typedef struct sr_params {
 } sr_params;
 
 /* One lattice of a batch (sr_create_batch): its own side, Hamiltonian,
- * temperature, seed, initial spins and rates; the region shape and every
- * other setting come from the sr_params given with the batch. */
+ * temperature, seed, initial spins, rates and, optionally, region shape (the
+ * partition of §5 into subsets G_i); every other setting comes from the
+ * sr_params given with the batch. */
 typedef struct sr_replica {
-  int L;                        /* side, a multiple of region_w and region_h, >= 3 */
+  int L;                        /* side, a multiple of the region extents, >= 3 */
   double J, h, T;               /* Eq. 2.1 and the temperature of Eq. 2.2 / 2.3 */
   uint64_t seed;                /* Philox key of this lattice's draws and fair-coin spins */
   int init_mode;                /* SR_INIT_* */
   int rates;                    /* SR_RATES_* */
+  int region_w, region_h;       /* this lattice's region extents (each <= 32); 0 = the batch's
+                                   common sr_params.region_w / region_h.  The rate grid follows
+                                   the shape: F = 63 - bitlen(w h) */
 } sr_replica;
 
 /* Observables and counters (reduced over all regions at the committed time). */
@@ -238,27 +242,41 @@ typedef struct sr_adapt {
 int sr_run_batch_adaptive(sr_ctx* ctx, const double* t_end, const sr_adapt* opts, double* last_tw);
 
 /* ---- autotuner ----
- * Chooses, for a batch of lattices, the region shape (among 8x8, 16x16,
- * 32x32, 16x8 and 32x16 that divide every L), the region lanes per warp
- * (automatic, 8, 16, 32) and kappa (4, 8, 16, 32) by timing trial runs of the real
- * lattices: each trial creates a context, runs the adaptive runner untimed to
- * t_trial / 2, then timed to t_trial, and scores committed flips per second.
- * One coordinate at a time (shape, then kappa, then lanes per warp).  The
- * trajectory of a lattice depends on its region shape (its random streams
- * are per region) but not on the other two choices.  common supplies every
- * other setting (as in sr_create_batch; region_w / region_h ignored).
- * t_trial > 0; 0 = 1.0.  Blocks until done; allocates and frees contexts.
- * Errors: those of sr_create_batch and sr_run_batch_adaptive; SR_EUNSUPPORTED
- * when no candidate shape divides every L. */
+ * Chooses, for a batch of lattices, the region shape of every lattice, the
+ * region lanes per warp (automatic, 8, 16, 32) and kappa (4, 8, 16, 32) by
+ * timing trial runs of the real lattices.  A warm-up run (the first of the
+ * shapes below that divides every L, to t = 8 t_trial) measures each
+ * lattice's committed events per site per unit time rho_b over its second
+ * half and keeps the spins it ends with; every trial starts from those
+ * spins (the coarsened configurations of a long run, not the first quench
+ * from the initial spins), runs the adaptive runner untimed to t_trial / 2,
+ * then timed to t_trial, and scores committed flips per second.  One
+ * coordinate at a time:
+ *   1. one shape for every lattice, among 8x8, 16x8, 16x16, 32x16 and 32x32;
+ *   2. a shape per lattice: the largest of those shapes (dividing L_b) with
+ *      rho_b x sites <= R, else the smallest, for R in {32, 64, 128, 256}.
+ *      A lattice's chain of iterations per unit time grows with the events
+ *      per region (§6: the cost of a step grows with f and g), so small
+ *      regions shorten the hot lattices' chains and large regions keep the
+ *      cold ones' boundary traffic low;
+ *   3. kappa, then 4. lanes per warp, with the best assignment.
+ * The trajectory of a lattice depends on its region shape (its random streams
+ * are per region) but not on the other choices.  common supplies every other
+ * setting (as in sr_create_batch; shapes in reps and common are ignored).
+ * t_trial > 0; 0 = 1.0.  region_wh (host, 2 n ints, may be NULL) receives
+ * each lattice's chosen (w, h).  Blocks until done; allocates and frees
+ * contexts.  Errors: those of sr_create_batch and sr_run_batch_adaptive;
+ * SR_EUNSUPPORTED when no candidate shape divides every L. */
 typedef struct sr_tune {
-  int region_w, region_h;       /* chosen region shape */
+  int region_w, region_h;       /* chosen region shape of lattice 0 */
   int lanes_per_warp;           /* chosen region lanes per warp (0 = automatic) */
   double kappa;                 /* chosen target events per region per window */
   double flips_per_s;           /* trial throughput of the choice */
   int trials;                   /* configurations timed */
+  double rate_threshold;        /* R of step 2 when a shape per lattice won, else 0 */
 } sr_tune;
 int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t_trial,
-                sr_tune* out);
+                sr_tune* out, int* region_wh);
 
 /* ---- score function (differentiation) ----
  * A path of the chain of §3 on [0, t_c] has log-likelihood

@@ -48,12 +48,13 @@ class _Params(C.Structure):
 
 class _Replica(C.Structure):
     _fields_ = [("L", C.c_int), ("J", C.c_double), ("h", C.c_double), ("T", C.c_double),
-                ("seed", C.c_uint64), ("init_mode", C.c_int), ("rates", C.c_int)]
+                ("seed", C.c_uint64), ("init_mode", C.c_int), ("rates", C.c_int),
+                ("region_w", C.c_int), ("region_h", C.c_int)]
 
 
 @dataclass
 class Replica:
-    """One lattice of a Batch."""
+    """One lattice of a Batch; region = None takes the batch's region shape."""
     L: int
     J: float = 1.0
     h: float = 0.0
@@ -61,6 +62,7 @@ class Replica:
     seed: int = 1
     init: str = "fair"
     rates: str = "metropolis"
+    region: Optional[Tuple[int, int]] = None
 
 
 class _Adapt(C.Structure):
@@ -70,7 +72,8 @@ class _Adapt(C.Structure):
 
 class _Tune(C.Structure):
     _fields_ = [("region_w", C.c_int), ("region_h", C.c_int), ("lanes_per_warp", C.c_int),
-                ("kappa", C.c_double), ("flips_per_s", C.c_double), ("trials", C.c_int)]
+                ("kappa", C.c_double), ("flips_per_s", C.c_double), ("trials", C.c_int),
+                ("rate_threshold", C.c_double)]
 
 
 class _Obs(C.Structure):
@@ -161,7 +164,7 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_score_stats": (C.c_int, [_P, C.c_int, _P, _P]),
             "sr_score_grad": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]),
             "sr_autotune": (C.c_int, [_P, C.c_int, C.POINTER(_Params), C.c_double,
-                                      C.POINTER(_Tune)]),
+                                      C.POINTER(_Tune), _P]),
             "sr_checkpoint_size": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
             "sr_checkpoint_save": (C.c_int, [_P, _P, C.c_size_t]),
             "sr_checkpoint_load": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
@@ -404,18 +407,28 @@ def _common_params(region, capacity=0, max_iters=0, lanes_per_region=0, lanes_pe
 def _replica_array(replicas):
     reps = [r if isinstance(r, Replica) else Replica(**r) for r in replicas]
     arr = (_Replica * len(reps))(*[
-        _Replica(r.L, r.J, r.h, r.T, r.seed, INIT_MODES[r.init], RATES[r.rates]) for r in reps])
+        _Replica(r.L, r.J, r.h, r.T, r.seed, INIT_MODES[r.init], RATES[r.rates],
+                 *(r.region if r.region else (0, 0))) for r in reps])
     return reps, arr
 
 
 @dataclass
 class Tuning:
-    """Choice of the autotuner (sr_autotune)."""
+    """Choice of the autotuner (sr_autotune): a region shape per lattice
+    (shapes[b]; region is lattice 0's), lanes per warp and kappa."""
     region: Tuple[int, int]
     lanes_per_warp: int
     kappa: float
     flips_per_s: float
     trials: int
+    rate_threshold: float
+    shapes: list
+
+    def replicas(self, replicas) -> list:
+        """The lattices with their chosen region shapes, for Batch(...)."""
+        reps = [r if isinstance(r, Replica) else Replica(**r) for r in replicas]
+        return [Replica(r.L, r.J, r.h, r.T, r.seed, r.init, r.rates, tuple(s))
+                for r, s in zip(reps, self.shapes)]
 
 
 def autotune(replicas, t_trial: float = 1.0, **settings) -> Tuning:
@@ -428,9 +441,12 @@ def autotune(replicas, t_trial: float = 1.0, **settings) -> Tuning:
         stream = _torch_stream()
     prm = _common_params((16, 16), stream=stream, **settings)
     t = _Tune()
-    _check(lib.sr_autotune(C.cast(arr, C.c_void_p), len(arr), C.byref(prm), t_trial, C.byref(t)),
-           "sr_autotune")
-    return Tuning((t.region_w, t.region_h), t.lanes_per_warp, t.kappa, t.flips_per_s, t.trials)
+    wh = np.zeros(2 * len(arr), dtype=np.int32)
+    _check(lib.sr_autotune(C.cast(arr, C.c_void_p), len(arr), C.byref(prm), t_trial, C.byref(t),
+                           _ptr(wh)), "sr_autotune")
+    shapes = [(int(wh[2 * b]), int(wh[2 * b + 1])) for b in range(len(arr))]
+    return Tuning((t.region_w, t.region_h), t.lanes_per_warp, t.kappa, t.flips_per_s, t.trials,
+                  t.rate_threshold, shapes)
 
 
 class Batch:
@@ -568,9 +584,15 @@ class Batch:
         _check(library().sr_score_stats(self._ctx, b, _ptr(c), _ptr(occ)), "sr_score_stats")
         return c, occ
 
+    def region_of(self, b: int) -> Tuple[int, int]:
+        """The region shape of lattice b."""
+        r = self.replicas[b]
+        return tuple(r.region) if r.region else tuple(self.region)
+
     def carry(self, b: int):
         r = self.replicas[b]
-        n = (r.L // self.region[0]) * (r.L // self.region[1])
+        W, H = self.region_of(b)
+        n = (r.L // W) * (r.L // H)
         i = np.zeros(n, dtype=np.uint64)
         x = np.zeros(n, dtype=np.float64)
         bb = np.zeros(n, dtype=np.float64)

@@ -109,19 +109,55 @@ __device__ void fill_warp(const KParams& p, bool want, int r, uint32_t loc, uint
   if (want) p.rhi[r] = to;
 }
 
-// Task queue of the asynchronous schedule: a task is (kind, lattice, chunk of
-// `chunk` consecutive regions); kinds 0 = pass, 1 = commit.  The publishing
-// thread has made the lattice's state visible first (fence).
-constexpr unsigned long long kTaskValid = 1ull << 62;
+// Task queue of the asynchronous schedule: a ring of qcap slots; ticket t
+// (the t-th task published, and the t-th claim) lives in slot t mod qcap.  A
+// task is (kind, lattice, chunk of `chunk` consecutive regions); kinds 0 =
+// pass, 1 = commit.  Every item carries the low 20 bits of its ticket; a
+// consumer takes only the item of its own ticket (qcap is odd, so an item of
+// an earlier lap never carries the tag of the slot's current ticket) and
+// clears it by compare-and-swap.  The items of a set are written one by one
+// after their tickets are reserved, and a slow publisher (many chunks, a busy
+// GPU) can find a slot still holding the item of the ticket one lap earlier,
+// not yet taken: an item is therefore written only into an empty slot
+// (compare-and-swap), waiting, within the bounded wait of SR_TIMEOUT, for the
+// earlier one to be taken.  No item is ever overwritten, lost or taken twice.
+// The publishing thread has made the lattice's state visible first (fence).
+__host__ __device__ constexpr unsigned long long task_item(unsigned kind, unsigned b, unsigned c,
+                                                           unsigned long long ticket) {
+  return kTaskValid | ((unsigned long long)(kind & 1u) << 62) | ((unsigned long long)b << 42) |
+         ((unsigned long long)c << 20) | (ticket & kTaskTag);
+}
+
+// Polling reads of words that other SMs write during the launch: the slot by
+// an atomic (performed at L2, always current: a warp polling its own slot
+// keeps the line hot in its SM's L1), the scheduler words by loads that bypass L1.
+__device__ __forceinline__ unsigned long long poll_slot(unsigned long long* a) {
+  return atomicOr(a, 0ull);
+}
+__device__ __forceinline__ unsigned long long poll_word(const unsigned long long* a) { return __ldcg(a); }
+__device__ __forceinline__ unsigned poll_word(const unsigned* a) { return __ldcg(a); }
+
 __device__ void enqueue_lattice(const KParams& p, int b, unsigned kind, int chunk) {
   const int nreg = p.reps[b].NR;
   const unsigned long long nch = (unsigned long long)((nreg + chunk - 1) / chunk);
   __threadfence();
   const unsigned long long base = atomicAdd(&p.st->qtail, nch);
   for (unsigned long long c = 0; c < nch; ++c) {
-    const unsigned long long item = kTaskValid | ((unsigned long long)kind << 60) |
-                                    ((unsigned long long)b << 32) | c;
-    atomicExch(&p.q[(base + c) % p.qcap], item);
+    const unsigned long long t = base + c;
+    const unsigned long long item = task_item(kind, (unsigned)b, (unsigned)c, t);
+    unsigned long long* slot = &p.q[t % p.qcap];
+    if (atomicCAS(slot, 0ull, item) == 0ull) continue;
+    const long long t0 = clock64();
+    unsigned nap = 32u;
+    while (atomicCAS(slot, 0ull, item) != 0ull) {
+      if (clock64() - t0 > p.timeout_cycles) {
+        atomicOr(&p.st->status, ST_TIMEOUT);
+        atomicOr(&p.st->cwork, 1ull << 63);
+        return;
+      }
+      __nanosleep(nap);
+      if (nap < 1024u) nap *= 2u;
+    }
   }
 }
 
@@ -231,19 +267,24 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
     for (;;) {
       unsigned long long item = 0ull;
       if (lane == 0) {
-        const unsigned long long slot = atomicAdd(&st->qhead, 1ull) % p.qcap;
+        const unsigned long long ticket = atomicAdd(&st->qhead, 1ull);
+        const unsigned long long slot = ticket % p.qcap;
         // the wait ends with SR_TIMEOUT only after a whole timeout in which no
         // task was published anywhere: when one small lattice is left, the
         // waiting warps are served a few per iteration, in the order they came
         long long tw0 = clock64();
-        unsigned long long seen = *(volatile unsigned long long*)&st->qtail;
+        unsigned long long seen = poll_word(&st->qtail);
+        // idle warps back off (64 ns doubling to 2 us) so that their polls do
+        // not crowd the memory system of the warps that work
+        unsigned nap = 64u;
         for (;;) {
-          item = *(volatile unsigned long long*)&p.q[slot];
-          if (item) break;
-          if (*(volatile unsigned*)&st->active == 0u) break;           // all lattices done
-          if (*(volatile unsigned*)&st->status & ST_TIMEOUT) break;
-          if (*(volatile unsigned long long*)&st->cwork == kCworkStop) break;  // stopped, drained
-          const unsigned long long qt = *(volatile unsigned long long*)&st->qtail;
+          item = poll_slot(&p.q[slot]);
+          if (item && (item & kTaskTag) == (ticket & kTaskTag)) break;   // this ticket's task
+          item = 0ull;
+          if (poll_word(&st->active) == 0u) break;                     // all lattices done
+          if (poll_word(&st->status) & ST_TIMEOUT) break;
+          if (poll_word(&st->cwork) == kCworkStop) break;              // stopped, drained
+          const unsigned long long qt = poll_word(&st->qtail);
           if (qt != seen) {
             seen = qt;
             tw0 = clock64();
@@ -252,24 +293,25 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
             stop_all(ST_TIMEOUT);
             break;
           }
-          __nanosleep(128);
+          __nanosleep(nap);
+          if (nap < 2048u) nap *= 2u;
         }
-        if (item) atomicExch(&p.q[slot], 0ull);
+        if (item) atomicCAS(&p.q[slot], item, 0ull);
         __threadfence();
       }
       item = __shfl_sync(0xFFFFFFFFu, item, 0);
       if (!item) break;
       __syncwarp();          // every lane's reads come after lane 0's acquire
-      const unsigned kind = (unsigned)((item >> 60) & 3ull);
-      const int b = (int)((item >> 32) & 0x0FFFFFFFull);
-      const int c = (int)(item & 0xFFFFFFFFull);
+      const unsigned kind = (unsigned)((item >> 62) & 1ull);
+      const int b = (int)((item >> 42) & 0xFFFFFull);
+      const int c = (int)((item >> 20) & 0x3FFFFFull);
       const RepDesc* d = p.reps + b;
       LatState* Ls = p.ls + b;
       const int loc = c * CH + lane;
       const bool mine = is_slot && lane < CH && loc < d->NR;
       const int r = d->off + loc;
       const unsigned cnt = (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, mine));
-      const unsigned w = *(volatile unsigned*)&Ls->w;
+      const unsigned w = poll_word(&Ls->w);
       RepStats* rs = p.rs + b;
       if (kind == 1u) {
         // ---- commit of window w (statement 3 of §4): the tentative state of
@@ -289,8 +331,9 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
           __threadfence();
           const unsigned old = atomicSub(&Ls->pend, cnt);
           if (old == cnt) {
+            __threadfence();
             const unsigned wn = w + 1u;
-            const unsigned n = Ls->n;                 // iterations of window w
+            const unsigned n = poll_word(&Ls->n);      // iterations of window w
             rs->windows += 1ull;
             rs->iterations += (unsigned long long)n;
             rs->last_iters = n;
@@ -302,14 +345,15 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
               p.win_iters[w % kWinRing] = n;
               p.win_iters[kWinRing + w % kWinRing] = fw;
             }
-            Ls->w = wn;
+            atomicExch(&Ls->w, wn);
             rs->windows_done = wn;
-            if (wn < (unsigned)d->nwin && !(*(volatile unsigned*)&st->status & kStop)) {
-              Ls->n = 1u;
-              Ls->chg = 0u;
-              Ls->ovf = 0u;
-              Ls->pend = (unsigned)d->NR;
-              Ls->ts = __dadd_rn(Ls->ts, d->Tw);
+            if (wn < (unsigned)d->nwin && !(poll_word(&st->status) & kStop)) {
+              atomicExch(&Ls->n, 1u);
+              atomicExch(&Ls->chg, 0u);
+              atomicExch(&Ls->ovf, 0u);
+              atomicExch(&Ls->pend, (unsigned)d->NR);
+              atomicExch((unsigned long long*)&Ls->ts, (unsigned long long)__double_as_longlong(
+                  __dadd_rn(__ldcg(&Ls->ts), d->Tw)));
               enqueue_lattice(p, b, 0u, CH);
             }
             __threadfence();
@@ -319,9 +363,9 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
         }
       } else {
         // ---- iteration n of window w; after an error no new passes run
-        if (*(volatile unsigned*)&st->status & kStop) continue;
-        const unsigned n = *(volatile unsigned*)&Ls->n;
-        const double t_s = *(volatile double*)&Ls->ts;
+        if (poll_word(&st->status) & kStop) continue;
+        const unsigned n = poll_word(&Ls->n);
+        const double t_s = __ldcg(&Ls->ts);
         const double t_end = __dadd_rn(t_s, d->Tw);
         Acc ra = {0u, 0u, 0u, 0u, 0u, 0u, false, false};
         if (mine) {
@@ -349,14 +393,14 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
           const unsigned old = atomicSub(&Ls->pend, cnt);
           if (old == cnt) {
             __threadfence();
-            const unsigned ch = *(volatile unsigned*)&Ls->chg;
-            const unsigned ov = *(volatile unsigned*)&Ls->ovf;
+            const unsigned ch = poll_word(&Ls->chg);
+            const unsigned ov = poll_word(&Ls->ovf);
             if (ov) {
               stop_all(ST_CAPACITY);
             } else if (!ch) {
               // no region of this lattice changed its lists: the fixed point;
               // commit tasks follow (the window's statistics count at their end)
-              Ls->pend = (unsigned)d->NR;
+              atomicExch(&Ls->pend, (unsigned)d->NR);
               const unsigned long long before = atomicAdd(&st->cwork, (unsigned long long)d->NR);
               if (before & kCworkStop)
                 atomicAdd(&st->cwork, 0ull - (unsigned long long)d->NR);   // stopped: no commit
@@ -364,10 +408,10 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
                 enqueue_lattice(p, b, 1u, CH);
             } else if ((int)n >= p.max_iters) {
               stop_all(ST_NOT_CONVERGED);
-            } else if (!(*(volatile unsigned*)&st->status & kStop)) {
-              Ls->n = n + 1u;
-              Ls->chg = 0u;
-              Ls->pend = (unsigned)d->NR;
+            } else if (!(poll_word(&st->status) & kStop)) {
+              atomicExch(&Ls->n, n + 1u);
+              atomicExch(&Ls->chg, 0u);
+              atomicExch(&Ls->pend, (unsigned)d->NR);
               enqueue_lattice(p, b, 0u, CH);
             }
           }
@@ -552,12 +596,14 @@ __global__ void init_rows_kernel(KParams p, int rep) {
   const int mode = p.reps[lt.rep].init_mode;
   const int rx = lt.loc % lt.NX, ry = lt.loc / lt.NX;
   uint32_t word = 0;
-  if (mode == SR_INIT_ALL_UP) {
-    word = (p.W == 32) ? 0xFFFFFFFFu : ((1u << p.W) - 1u);
+  if (y >= lt.H) {
+    // rows past the lattice's region height stay empty
+  } else if (mode == SR_INIT_ALL_UP) {
+    word = (lt.W == 32) ? 0xFFFFFFFFu : ((1u << lt.W) - 1u);
   } else if (mode == SR_INIT_FAIR_COIN) {
-    const uint32_t gy = (uint32_t)(ry * p.H + y);
-    for (int x = 0; x < p.W; ++x) {
-      const uint32_t site = gy * (uint32_t)lt.L + (uint32_t)(rx * p.W + x);
+    const uint32_t gy = (uint32_t)(ry * lt.H + y);
+    for (int x = 0; x < lt.W; ++x) {
+      const uint32_t site = gy * (uint32_t)lt.L + (uint32_t)(rx * lt.W + x);
       uint32_t w[4];
       philox4x32_10(site, 0u, 0u, 1u, lt.key0, lt.key1, w);
       word |= (w[0] & 1u) << x;
@@ -570,13 +616,13 @@ __global__ void init_rows_kernel(KParams p, int rep) {
 __global__ void pack_rows_kernel(KParams p, int b, const int8_t* spins) {
   const RepDesc& d = p.reps[b];
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)d.NR * p.H) return;
+  if (t >= (size_t)d.NR * d.H) return;
   const int loc = (int)(t % d.NR), y = (int)(t / d.NR);
   const int r = d.off + loc;
   const int rx = loc % d.NX, ry = loc / d.NX;
-  const size_t base = (size_t)(ry * p.H + y) * d.L + (size_t)rx * p.W;
+  const size_t base = (size_t)(ry * d.H + y) * d.L + (size_t)rx * d.W;
   uint32_t word = 0;
-  for (int x = 0; x < p.W; ++x) word |= (uint32_t)(spins[base + x] > 0) << x;
+  for (int x = 0; x < d.W; ++x) word |= (uint32_t)(spins[base + x] > 0) << x;
   p.rows[(size_t)y * p.NR + r] = word;
 }
 
@@ -586,9 +632,9 @@ __global__ void unpack_rows_kernel(KParams p, int b, int8_t* spins) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)d.L * d.L) return;
   const int gx = (int)(t % d.L), gy = (int)(t / d.L);
-  const int r = d.off + (gy / p.H) * d.NX + gx / p.W;
-  const uint32_t word = p.rows[((size_t)p.rcidx[r] * p.H + gy % p.H) * p.NR + r];
-  spins[t] = ((word >> (gx % p.W)) & 1u) ? 1 : -1;
+  const int r = d.off + (gy / d.H) * d.NX + gx / d.W;
+  const uint32_t word = p.rows[((size_t)p.rcidx[r] * p.H + gy % d.H) * p.NR + r];
+  spins[t] = ((word >> (gx % d.W)) & 1u) ? 1 : -1;
 }
 
 // Clock state at t = 0 of every region of lattice `rep` (every lattice when
@@ -625,17 +671,18 @@ __global__ void observe_ints_kernel(KParams p, int b, long long* out2) {
   if (loc < d.NR) {
     const int r = d.off + loc;
     const size_t nr = (size_t)p.NR;
-    const uint32_t wmask = (p.W == 32) ? 0xFFFFFFFFu : ((1u << p.W) - 1u);
+    const int W = d.W, H = d.H;
+    const uint32_t wmask = (W == 32) ? 0xFFFFFFFFu : ((1u << W) - 1u);
     const uint32_t* rows_c = p.rows + (size_t)p.rcidx[r] * p.H * nr;
     const uint32_t hS = p.halo[1 * nr + r], hE = p.halo[3 * nr + r];
-    for (int y = 0; y < p.H; ++y) {
+    for (int y = 0; y < H; ++y) {
       const uint32_t rw = rows_c[(size_t)y * nr + r];
-      const uint32_t dn = (y < p.H - 1) ? rows_c[(size_t)(y + 1) * nr + r]
-                                        : (d.spans_y ? rows_c[r] : hS);
+      const uint32_t dn = (y < H - 1) ? rows_c[(size_t)(y + 1) * nr + r]
+                                      : (d.spans_y ? rows_c[r] : hS);
       const uint32_t rbit = d.spans_x ? (rw & 1u) : (hE >> y) & 1u;
-      const uint32_t rt = (rw >> 1) | (rbit << (p.W - 1));
-      mag += 2 * __popc(rw) - p.W;
-      bonds += (p.W - 2 * __popc((rw ^ rt) & wmask)) + (p.W - 2 * __popc((rw ^ dn) & wmask));
+      const uint32_t rt = (rw >> 1) | (rbit << (W - 1));
+      mag += 2 * __popc(rw) - W;
+      bonds += (W - 2 * __popc((rw ^ rt) & wmask)) + (W - 2 * __popc((rw ^ dn) & wmask));
     }
   }
   for (int o = 16; o > 0; o >>= 1) {

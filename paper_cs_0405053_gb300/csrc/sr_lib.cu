@@ -39,8 +39,8 @@ struct sr_ctx {
   RepDesc* hdesc;               // [nrep] host copy of the descriptors
   double* t_c;                  // [nrep] committed time of each lattice
   unsigned* wins;               // [nrep] committed windows of each lattice
-  int NR, F, Lmax;
-  double scale;
+  int NR, Lmax;
+  int Wmax, Hmax;               // the largest region shape of any lattice (layout of the state)
   cudaStream_t stream;
   bool own_stream;
   int num_sms;
@@ -155,8 +155,8 @@ void score_tables(const sr_replica& p, double* tab) {
 KParams make_params(const sr_ctx* c) {
   KParams k;
   std::memset(&k, 0, sizeof k);
-  k.W = c->prm.region_w;
-  k.H = c->prm.region_h;
+  k.W = c->Wmax;
+  k.H = c->Hmax;
   k.NR = c->NR;
   k.nrep = c->nrep;
   k.reps = c->desc;
@@ -172,8 +172,6 @@ KParams make_params(const sr_ctx* c) {
   k.ls = c->ls;
   k.q = c->q;
   k.qcap = c->qcap;
-  k.scale = c->scale;
-  k.F = c->F;
   k.rows = c->rows;
   k.halo = c->halo;
   k.ci = c->ci;
@@ -339,8 +337,7 @@ int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
       hls[b].ts = c->t_c[b];
       if (nwin[b] <= 0) continue;
       const int nch = (c->hdesc[b].NR + c->lanes - 1) / c->lanes;
-      for (int ch = 0; ch < nch; ++ch)
-        items[t++] = kTaskValid | ((unsigned long long)b << 32) | (unsigned long long)ch;
+      for (int ch = 0; ch < nch; ++ch, ++t) items[t] = task_item(0u, (unsigned)b, (unsigned)ch, t);
     }
     int rca = cuda_rc(cudaMemcpyAsync(c->ls, hls, (size_t)c->nrep * sizeof(LatState),
                                       cudaMemcpyHostToDevice, c->stream));
@@ -397,7 +394,7 @@ int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
 // per region (every p_k <= 1), with a margin; events past the ring are drawn on
 // the fly, so the cap only bounds memory.
 int ring_length(const sr_ctx* c, double Tw) {
-  const double want = 1.25 * (double)c->prm.region_w * c->prm.region_h * Tw + 16.0;
+  const double want = 1.25 * (double)c->Wmax * c->Hmax * Tw + 16.0;
   int K = 16;
   while (K < want && K < 4096) K *= 2;
   return K;
@@ -442,7 +439,12 @@ void free_all(sr_ctx* c) {
   std::free(c->wins);
 }
 
+// The region shape of lattice r: its own, or the batch's common one.
+int shape_w(const sr_replica& r, const sr_params& p) { return r.region_w > 0 ? r.region_w : p.region_w; }
+int shape_h(const sr_replica& r, const sr_params& p) { return r.region_h > 0 ? r.region_h : p.region_h; }
+
 int check_replica(const sr_replica& r, int W, int H) {
+  if (W < 1 || H < 1) return SR_EINVAL;
   if (r.L < 3 || r.L % W || r.L % H) return SR_EINVAL;
   if (!(r.T > 0.0) || !std::isfinite(r.J) || !std::isfinite(r.h) || std::isnan(r.T)) return SR_EINVAL;
   if (r.init_mode < SR_INIT_FAIR_COIN || r.init_mode > SR_INIT_ALL_DOWN) return SR_EINVAL;
@@ -470,7 +472,10 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   if (p.score && p.lanes_per_region == 32) return SR_EUNSUPPORTED;
   if (p.region_w > 32 || p.region_h > 32) return SR_EUNSUPPORTED;
   for (int b = 0; b < n; ++b) {
-    const int rc = check_replica(reps[b], p.region_w, p.region_h);
+    if (reps[b].region_w < 0 || reps[b].region_h < 0) return SR_EINVAL;
+    const int W = shape_w(reps[b], p), H = shape_h(reps[b], p);
+    if (W > 32 || H > 32) return SR_EUNSUPPORTED;
+    const int rc = check_replica(reps[b], W, H);
     if (rc != SR_OK) return rc;
   }
   sr_ctx* c = (sr_ctx*)std::calloc(1, sizeof(sr_ctx));
@@ -488,13 +493,18 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     std::free(c);
     return SR_ENOMEM;
   }
-  const int W = p.region_w, H = p.region_h;
-  c->F = 63 - bitlen((long long)W * H);
-  c->scale = std::ldexp(1.0, -c->F);
   long long total = 0;
   for (int b = 0; b < n; ++b) {
     c->reps[b] = reps[b];
     RepDesc& d = c->hdesc[b];
+    const int W = shape_w(reps[b], p), H = shape_h(reps[b], p);
+    d.W = W;
+    d.H = H;
+    if (W > c->Wmax) c->Wmax = W;
+    if (H > c->Hmax) c->Hmax = H;
+    // the rate grid of Eq. 3.3 for this shape: Lambda = sum_k N_k P_k fits 64 bits
+    d.F = 63 - bitlen((long long)W * H);
+    d.scale = std::ldexp(1.0, -d.F);
     d.L = reps[b].L;
     d.NX = d.L / W;
     d.NY = d.L / H;
@@ -505,7 +515,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     d.key0 = (uint32_t)reps[b].seed;
     d.key1 = (uint32_t)(reps[b].seed >> 32);
     d.init_mode = reps[b].init_mode;
-    rate_table(reps[b], c->F, d.P);
+    rate_table(reps[b], d.F, d.P);
     for (int k = 0; k < 10; ++k) d.Rp[k] = d.P[k] ? ~0ull / d.P[k] : 0ull;
     total += d.NR;
     if (d.L > c->Lmax) c->Lmax = d.L;
@@ -575,7 +585,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     if (wpb > SR_LANE_MAX_THREADS / 32) wpb = SR_LANE_MAX_THREADS / 32;
     c->rl = wpb * lanes;
     c->tpb = 32 * wpb;
-    c->smem = lane_smem_bytes(H, c->rl, p.score != 0);
+    c->smem = lane_smem_bytes(c->Hmax, c->rl, p.score != 0);
   }
   {
     const void* fn = relax_fn(c->mode, 0, gen_features(p));
@@ -604,6 +614,17 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
                        : (p.schedule == 2 ||
                           (p.schedule == 0 && (n > 1 || (long long)c->NR > (long long)blocks * c->rl)))
                              ? 1 : 0;
+    // the task items of the asynchronous schedule hold the lattice and chunk in 20 and 22 bits
+    if (c->dynamic == 2) {
+      bool fits = n < kTaskMaxLattices;
+      for (int b = 0; b < n && fits; ++b)
+        fits = (c->hdesc[b].NR + c->lanes - 1) / c->lanes < kTaskMaxChunks;
+      if (!fits) {
+        free_all(c);
+        std::free(c);
+        return SR_EUNSUPPORTED;
+      }
+    }
     if (c->dynamic) {
       // the dynamic instance: same launch bounds; check it fits the same grid
       const void* fd = relax_fn(c->mode, c->dynamic, gen_features(p));
@@ -621,7 +642,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
 
   int rc = SR_OK;
   const size_t nr = (size_t)c->NR;
-  rc |= dalloc(&c->rows, 2 * (size_t)H * nr);
+  rc |= dalloc(&c->rows, 2 * (size_t)c->Hmax * nr);
   rc |= dalloc(&c->halo, 4 * nr);
   rc |= dalloc(&c->ci, 2 * nr);
   rc |= dalloc(&c->cx, 2 * nr);
@@ -657,7 +678,13 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
     unsigned long long chunks = 0ull;
     for (int b = 0; b < n; ++b)
       chunks += (unsigned long long)((c->hdesc[b].NR + c->lanes - 1) / c->lanes);
+    // a ring far larger than what can be outstanding at once (one task set per
+    // lattice, one claim per warp), so that a slot is rarely still full when
+    // its next lap comes; odd, so that an item of an earlier lap never carries
+    // the tag of the slot's current ticket
     c->qcap = chunks + (unsigned long long)c->blocks * (unsigned long long)(c->tpb / 32) + 64ull;
+    c->qcap = 4ull * c->qcap < (1ull << 20) ? (1ull << 20) : 4ull * c->qcap;
+    c->qcap |= 1ull;
     rc |= dalloc(&c->ls, (size_t)n);
     rc |= dalloc(&c->q, (size_t)c->qcap);
   }
@@ -670,7 +697,7 @@ int create_common(sr_ctx** out, const sr_replica* reps, int n, const sr_params& 
   c->CB = (c->mode == 1 || p.replay_records < 0 || p.score) ? 0
                                                            : (p.replay_records ? p.replay_records : 64);
   if (c->CB > 0) {
-    rc |= dalloc(&c->log, nr * (size_t)c->CB * (size_t)(kRecHead + H));
+    rc |= dalloc(&c->log, nr * (size_t)c->CB * (size_t)(kRecHead + c->Hmax));
     rc |= dalloc(&c->loghdr, nr * 4);
   }
   if (p.trace_capacity > 0) {
@@ -870,13 +897,14 @@ int carry_of(sr_ctx* c, int b, uint64_t* index, double* x, double* bb, double* t
 // A checkpoint in host memory: a header, one record per lattice, then each
 // state array as [m][NR] (the committed copy of every region), in the order
 // rows, ci, cx, ckv, cb, ct, cim, cib and, in score mode, sc, si.
-constexpr uint64_t kCkptTag = 0x31305450434b5253ull;   // "SRKCPT01" read as bytes
+constexpr uint64_t kCkptTag = 0x32305450434b5253ull;   // "SRKCPT02" read as bytes
 struct CkptHeader {
   uint64_t tag;
   int32_t nrep, NR, W, H, score, fresh;
 };
 struct CkptRep {
   int32_t L, rates;
+  int32_t W, H;                 // the lattice's region shape
   uint64_t seed;
   double J, h, T, t_c;
   uint32_t wins, pad;
@@ -884,7 +912,7 @@ struct CkptRep {
 };
 
 size_t ckpt_bytes(const sr_ctx* c) {
-  const size_t nr = (size_t)c->NR, H = (size_t)c->prm.region_h;
+  const size_t nr = (size_t)c->NR, H = (size_t)c->Hmax;
   size_t b = sizeof(CkptHeader) + (size_t)c->nrep * sizeof(CkptRep);
   b += H * nr * sizeof(uint32_t);                     // spin rows
   b += 7 * nr * 8;                                    // ci, cx, ckv, cb, ct, cim, cib
@@ -925,7 +953,7 @@ int ckpt_push(sr_ctx* c, T* dev, size_t m, const unsigned char*& in) {
 }
 
 int ckpt_save(sr_ctx* c, unsigned char* out) {
-  const size_t nr = (size_t)c->NR, H = (size_t)c->prm.region_h;
+  const size_t nr = (size_t)c->NR, H = (size_t)c->Hmax;
   std::vector<uint8_t> cidx(nr);
   std::vector<RepStats> rs((size_t)c->nrep);
   if (cudaMemcpyAsync(cidx.data(), c->rcidx, nr, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -938,8 +966,8 @@ int ckpt_save(sr_ctx* c, unsigned char* out) {
   hd.tag = kCkptTag;
   hd.nrep = c->nrep;
   hd.NR = c->NR;
-  hd.W = c->prm.region_w;
-  hd.H = c->prm.region_h;
+  hd.W = c->Wmax;
+  hd.H = c->Hmax;
   hd.score = c->prm.score ? 1 : 0;
   hd.fresh = c->prm.fresh_steps ? 1 : 0;
   std::memcpy(out, &hd, sizeof hd);
@@ -949,6 +977,8 @@ int ckpt_save(sr_ctx* c, unsigned char* out) {
     std::memset(&cr, 0, sizeof cr);
     cr.L = c->reps[b].L;
     cr.rates = c->reps[b].rates;
+    cr.W = c->hdesc[b].W;
+    cr.H = c->hdesc[b].H;
     cr.seed = c->reps[b].seed;
     cr.J = c->reps[b].J;
     cr.h = c->reps[b].h;
@@ -976,8 +1006,8 @@ int ckpt_save(sr_ctx* c, unsigned char* out) {
 bool ckpt_matches(const sr_ctx* c, const unsigned char* in) {
   CkptHeader hd;
   std::memcpy(&hd, in, sizeof hd);
-  if (hd.tag != kCkptTag || hd.nrep != c->nrep || hd.NR != c->NR || hd.W != c->prm.region_w ||
-      hd.H != c->prm.region_h || hd.score != (c->prm.score ? 1 : 0) ||
+  if (hd.tag != kCkptTag || hd.nrep != c->nrep || hd.NR != c->NR || hd.W != c->Wmax ||
+      hd.H != c->Hmax || hd.score != (c->prm.score ? 1 : 0) ||
       hd.fresh != (c->prm.fresh_steps ? 1 : 0))
     return false;
   in += sizeof hd;
@@ -985,7 +1015,8 @@ bool ckpt_matches(const sr_ctx* c, const unsigned char* in) {
     CkptRep cr;
     std::memcpy(&cr, in + (size_t)b * sizeof cr, sizeof cr);
     const sr_replica& r = c->reps[b];
-    if (cr.L != r.L || cr.rates != r.rates || cr.seed != r.seed || cr.J != r.J || cr.h != r.h ||
+    if (cr.L != r.L || cr.rates != r.rates || cr.W != c->hdesc[b].W || cr.H != c->hdesc[b].H ||
+        cr.seed != r.seed || cr.J != r.J || cr.h != r.h ||
         cr.T != r.T || !(cr.t_c >= 0.0) || !std::isfinite(cr.t_c))
       return false;
   }
@@ -993,7 +1024,7 @@ bool ckpt_matches(const sr_ctx* c, const unsigned char* in) {
 }
 
 int ckpt_load(sr_ctx* c, const unsigned char* in) {
-  const size_t nr = (size_t)c->NR, H = (size_t)c->prm.region_h;
+  const size_t nr = (size_t)c->NR, H = (size_t)c->Hmax;
   in += sizeof(CkptHeader);
   std::vector<CkptRep> cr((size_t)c->nrep);
   std::memcpy(cr.data(), in, cr.size() * sizeof(CkptRep));
@@ -1351,43 +1382,59 @@ int sr_run_batch_adaptive(sr_ctx* c, const double* t_end, const sr_adapt* opts, 
 }
 
 int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t_trial,
-                sr_tune* out) {
+                sr_tune* out, int* region_wh) {
   if (!reps || n < 1 || !common || !out) return SR_EINVAL;
   if (t_trial == 0.0) t_trial = 1.0;
   if (!(t_trial > 0.0) || !std::isfinite(t_trial)) return SR_EINVAL;
   std::memset(out, 0, sizeof *out);
-  const int shapes[5][2] = {{16, 16}, {8, 8}, {32, 32}, {16, 8}, {32, 16}};
-  bool ok[5];
-  int n_ok = 0;
-  for (int s = 0; s < 5; ++s) {
-    ok[s] = true;
+  // candidate shapes by area: 64, 128, 256, 512, 1024 sites
+  constexpr int kS = 5;
+  const int shapes[kS][2] = {{8, 8}, {16, 8}, {16, 16}, {32, 16}, {32, 32}};
+  auto fits = [&](int b, int s) {
+    return reps[b].L % shapes[s][0] == 0 && reps[b].L % shapes[s][1] == 0;
+  };
+  auto fits_all = [&](int s) {
     for (int b = 0; b < n; ++b)
-      if (reps[b].L % shapes[s][0] || reps[b].L % shapes[s][1]) ok[s] = false;
-    n_ok += ok[s];
-  }
-  if (n_ok == 0) return SR_EUNSUPPORTED;
-  double* te = (double*)std::malloc((size_t)n * sizeof(double));
-  if (!te) return SR_ENOMEM;
-  // one trial: committed flips per second over [t_trial / 2, t_trial]
-  auto trial = [&](int w, int h, int lpw, double kappa, double* score) -> int {
+      if (!fits(b, s)) return false;
+    return true;
+  };
+  std::vector<sr_replica> rr(reps, reps + n);
+  std::vector<int> sw((size_t)n), sh((size_t)n), best_w((size_t)n), best_h((size_t)n);
+  std::vector<double> te((size_t)n), rate((size_t)n, 0.0);
+  std::vector<unsigned long long> c0((size_t)n);
+  std::vector<size_t> soff((size_t)n + 1, 0);
+  for (int b = 0; b < n; ++b) soff[(size_t)b + 1] = soff[(size_t)b] + (size_t)reps[b].L * reps[b].L;
+  std::vector<int8_t> late;          // every lattice's spins at the end of the warm-up run
+  auto make = [&](int lpw, sr_ctx** c) -> int {
+    for (int b = 0; b < n; ++b) {
+      rr[(size_t)b].region_w = sw[(size_t)b];
+      rr[(size_t)b].region_h = sh[(size_t)b];
+    }
     sr_params p = *common;
-    p.region_w = w;
-    p.region_h = h;
+    p.region_w = sw[0];
+    p.region_h = sh[0];
     p.lanes_per_warp = lpw;
+    return create_common(c, rr.data(), n, p);
+  };
+  // one trial of a shape assignment from the warm-up run's spins: committed
+  // flips per second over [t_trial / 2, t_trial]
+  auto trial = [&](int lpw, double kappa, double* score) -> int {
     sr_ctx* c = nullptr;
-    int rc = create_common(&c, reps, n, p);
+    int rc = make(lpw, &c);
     if (rc != SR_OK) return rc;
+    for (int b = 0; b < n && rc == SR_OK; ++b)
+      rc = sr_set_spins_replica(c, b, late.data() + soff[(size_t)b], soff[(size_t)b + 1] - soff[(size_t)b]);
     sr_adapt o;
     std::memset(&o, 0, sizeof o);
     o.kappa = kappa;
     o.chunk = t_trial / 4.0;
-    for (int b = 0; b < n; ++b) te[b] = 0.5 * t_trial;
-    rc = sr_run_batch_adaptive(c, te, &o, nullptr);
+    for (int b = 0; b < n; ++b) te[(size_t)b] = 0.5 * t_trial;
+    if (rc == SR_OK) rc = sr_run_batch_adaptive(c, te.data(), &o, nullptr);
     unsigned long long before = 0, after = 0;
     for (int b = 0; b < n && rc == SR_OK; ++b) before += c->h_rs[b].committed;
     const auto t0 = std::chrono::steady_clock::now();
-    for (int b = 0; b < n; ++b) te[b] = t_trial;
-    if (rc == SR_OK) rc = sr_run_batch_adaptive(c, te, &o, nullptr);
+    for (int b = 0; b < n; ++b) te[(size_t)b] = t_trial;
+    if (rc == SR_OK) rc = sr_run_batch_adaptive(c, te.data(), &o, nullptr);
     const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (int b = 0; b < n && rc == SR_OK; ++b) after += c->h_rs[b].committed;
     sr_destroy(c);
@@ -1395,23 +1442,87 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
     out->trials += 1;
     return rc;
   };
-  int rc = SR_OK;
-  int bw = 0, bh = 0, blpw = 0;
-  double bk = 8.0, best = -1.0;
-  for (int s = 0; s < 5 && rc == SR_OK; ++s) {
-    if (!ok[s]) continue;
-    double sc = 0.0;
-    rc = trial(shapes[s][0], shapes[s][1], 0, bk, &sc);
-    if (rc == SR_OK && sc > best) {
-      best = sc;
-      bw = shapes[s][0];
-      bh = shapes[s][1];
-    }
+  double best = -1.0, bk = 8.0, bthr = 0.0;
+  int blpw = 0;
+  auto keep = [&](double sc) {
+    if (sc <= best) return false;
+    best = sc;
+    best_w = sw;
+    best_h = sh;
+    return true;
+  };
+  // 0. warm-up run in the first shape that divides every L, to t = 8 t_trial:
+  // each lattice's committed events per site per unit time over its second
+  // half, and its spins at the end
+  int s0 = -1;
+  for (int s = 0; s < kS && s0 < 0; ++s)
+    if (fits_all(s)) s0 = s;
+  if (s0 < 0) return SR_EUNSUPPORTED;     // no shape divides every L
+  for (int b = 0; b < n; ++b) {
+    sw[(size_t)b] = shapes[s0][0];
+    sh[(size_t)b] = shapes[s0][1];
   }
+  {
+    sr_ctx* c = nullptr;
+    int rc = make(0, &c);
+    if (rc != SR_OK) return rc;
+    sr_adapt o;
+    std::memset(&o, 0, sizeof o);
+    o.kappa = bk;
+    for (int b = 0; b < n; ++b) te[(size_t)b] = 4.0 * t_trial;
+    rc = sr_run_batch_adaptive(c, te.data(), &o, nullptr);
+    for (int b = 0; b < n && rc == SR_OK; ++b) c0[(size_t)b] = c->h_rs[b].committed;
+    for (int b = 0; b < n; ++b) te[(size_t)b] = 8.0 * t_trial;
+    if (rc == SR_OK) rc = sr_run_batch_adaptive(c, te.data(), &o, nullptr);
+    for (int b = 0; b < n && rc == SR_OK; ++b)
+      rate[(size_t)b] = (double)(c->h_rs[b].committed - c0[(size_t)b]) /
+                        ((double)reps[b].L * reps[b].L * 4.0 * t_trial);
+    if (rc == SR_OK) {
+      late.resize(soff[(size_t)n]);
+      for (int b = 0; b < n && rc == SR_OK; ++b)
+        rc = spins_host_of(c, b, late.data() + soff[(size_t)b], soff[(size_t)b + 1] - soff[(size_t)b]);
+    }
+    sr_destroy(c);
+    if (rc != SR_OK) return rc;
+  }
+  int rc = SR_OK;
+  // 1. one shape for every lattice
+  for (int s = 0; s < kS && rc == SR_OK; ++s) {
+    if (!fits_all(s)) continue;
+    for (int b = 0; b < n; ++b) {
+      sw[(size_t)b] = shapes[s][0];
+      sh[(size_t)b] = shapes[s][1];
+    }
+    double sc = 0.0;
+    rc = trial(0, bk, &sc);
+    if (rc == SR_OK && keep(sc)) bthr = 0.0;
+  }
+  // 2. a shape per lattice: the largest region whose expected events per unit
+  // time (rate per site x sites) stay below a threshold, so hot lattices get
+  // small regions (short chains of iterations) and cold ones large regions
+  // (few boundary events)
+  const double thresholds[4] = {32.0, 64.0, 128.0, 256.0};
+  for (int i = 0; i < 4 && rc == SR_OK; ++i) {
+    for (int b = 0; b < n; ++b) {
+      int pick = -1;          // the smallest fitting shape, or the largest under the threshold
+      for (int s = 0; s < kS; ++s)
+        if (fits(b, s) &&
+            (pick < 0 || rate[(size_t)b] * shapes[s][0] * shapes[s][1] <= thresholds[i]))
+          pick = s;
+      sw[(size_t)b] = shapes[pick][0];
+      sh[(size_t)b] = shapes[pick][1];
+    }
+    double sc = 0.0;
+    rc = trial(0, bk, &sc);
+    if (rc == SR_OK && keep(sc)) bthr = thresholds[i];
+  }
+  // 3. kappa, then 4. region lanes per warp, with the best assignment
   const double kappas[3] = {4.0, 16.0, 32.0};
   for (int i = 0; i < 3 && rc == SR_OK; ++i) {
+    sw = best_w;
+    sh = best_h;
     double sc = 0.0;
-    rc = trial(bw, bh, 0, kappas[i], &sc);
+    rc = trial(0, kappas[i], &sc);
     if (rc == SR_OK && sc > best) {
       best = sc;
       bk = kappas[i];
@@ -1419,20 +1530,27 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
   }
   const int lpws[3] = {8, 16, 32};
   for (int i = 0; i < 3 && rc == SR_OK; ++i) {
+    sw = best_w;
+    sh = best_h;
     double sc = 0.0;
-    rc = trial(bw, bh, lpws[i], bk, &sc);
+    rc = trial(lpws[i], bk, &sc);
     if (rc == SR_OK && sc > best) {
       best = sc;
       blpw = lpws[i];
     }
   }
-  std::free(te);
   if (rc != SR_OK) return rc;
-  out->region_w = bw;
-  out->region_h = bh;
+  out->region_w = best_w[0];
+  out->region_h = best_h[0];
   out->lanes_per_warp = blpw;
   out->kappa = bk;
   out->flips_per_s = best;
+  out->rate_threshold = bthr;
+  if (region_wh)
+    for (int b = 0; b < n; ++b) {
+      region_wh[2 * b] = best_w[(size_t)b];
+      region_wh[2 * b + 1] = best_h[(size_t)b];
+    }
   return SR_OK;
 }
 
@@ -1510,7 +1628,7 @@ int sr_get_info(sr_ctx* c, int* n_regions, int* frac_bits, uint64_t* P, int* thr
                 int* blocks) {
   if (!c) return SR_EINVAL;
   if (n_regions) *n_regions = c->hdesc[0].NR;
-  if (frac_bits) *frac_bits = c->F;
+  if (frac_bits) *frac_bits = c->hdesc[0].F;
   if (P)
     for (int k = 0; k < 10; ++k) P[k] = c->hdesc[0].P[k];
   if (threads_per_block) *threads_per_block = c->rl;
@@ -1566,7 +1684,7 @@ struct Carver {
 // every device pointer of c, in one fixed order, and returns the bytes used.
 // The size check and the real layout both run this one sequence.
 size_t noalloc_layout(sr_ctx& c, uintptr_t base) {
-  const size_t nr = (size_t)c.NR, H = (size_t)c.prm.region_h;
+  const size_t nr = (size_t)c.NR, H = (size_t)c.Hmax;
   Carver cv{base, 0};
   c.rows = cv.take<uint32_t>(2 * H * nr);
   c.halo = cv.take<uint32_t>(4 * nr);
@@ -1636,11 +1754,15 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   c.hdesc = &hd;
   c.t_c = &t_c;
   c.wins = &wins;
-  c.F = 63 - bitlen((long long)region_w * region_h);
-  c.scale = std::ldexp(1.0, -c.F);
+  c.Wmax = region_w;
+  c.Hmax = region_h;
   hd.L = L;
   hd.NX = L / region_w;
   hd.NY = L / region_h;
+  hd.W = region_w;
+  hd.H = region_h;
+  hd.F = 63 - bitlen((long long)region_w * region_h);
+  hd.scale = std::ldexp(1.0, -hd.F);
   hd.NR = hd.NX * hd.NY;
   hd.off = 0;
   hd.spans_x = hd.NX == 1;
@@ -1648,7 +1770,7 @@ extern "C" int sr_run_noalloc(int L, double J, double h, double T, int region_w,
   hd.key0 = (uint32_t)seed;
   hd.key1 = (uint32_t)(seed >> 32);
   hd.init_mode = SR_INIT_FAIR_COIN;
-  rate_table(rp, c.F, hd.P);
+  rate_table(rp, hd.F, hd.P);
   for (int k = 0; k < 10; ++k) hd.Rp[k] = hd.P[k] ? ~0ull / hd.P[k] : 0ull;
   c.NR = hd.NR;
   c.Lmax = L;

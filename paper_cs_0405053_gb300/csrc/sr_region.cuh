@@ -24,22 +24,25 @@ struct Acc {
 // them from the launch parameters.
 template <int SOFT>
 __device__ __forceinline__ double tau_any(double t_last, double x, double b, unsigned long long lam,
-                                          const KParams& p) {
-  return SOFT ? tau_soft(t_last, x, b, lam, p.F) : tau_hat(t_last, x, b, lam, p.scale);
+                                          const Lat& lt) {
+  return SOFT ? tau_soft(t_last, x, b, lam, lt.F) : tau_hat(t_last, x, b, lam, lt.scale);
 }
 template <int SOFT>
 __device__ __forceinline__ double accrue_any(double b, double tb, double tl, unsigned long long lam,
-                                             const KParams& p) {
-  return SOFT ? sf::add_pos(b, sf::mul_pos(sf::u64_scaled(lam, p.F), sf::sub_pos(tb, tl)))
-              : accrue(b, tb, tl, lam, p.scale);
+                                             const Lat& lt) {
+  return SOFT ? sf::add_pos(b, sf::mul_pos(sf::u64_scaled(lam, lt.F), sf::sub_pos(tb, tl)))
+              : accrue(b, tb, tl, lam, lt.scale);
 }
 
 template <int SOFT, bool GEN>
 __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, unsigned cidx,
                            double t_s, double t_end, unsigned wg, Region& g, Acc& acc) {
-  const int W = p.W, H = p.H, NR = p.NR;
+  // the lattice's region shape; per-region arrays are laid out for the launch's
+  // largest shape (p.H rows)
+  const int W = lt.W, H = lt.H, NR = p.NR, HL = p.H;
   const bool score = GEN && p.score, fresh = GEN && p.fresh;
   const int tcap = GEN ? p.tcap : 0;
+  g.set_shape(W, H);
   const int wp = n_iter & 1;
   const int rp = wp ^ 1;
   const int rx = lt.loc % lt.NX, ry = lt.loc / lt.NX;
@@ -146,7 +149,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   // break point depends only on the committed state and on its first m inputs.
   // Walk the new inputs against the inputs logged by the last pass; resume from
   // the checkpoint before the first difference.
-  const size_t rwords = (size_t)kRecHead + H;
+  const size_t rwords = (size_t)kRecHead + HL;
   uint32_t* rec0 = p.log + (size_t)r * p.CB * rwords;
   uint32_t* hdr = p.loghdr + (size_t)r * 4;     // breaks consumed, records kept, M0, bonds0
   unsigned m = 0;
@@ -214,7 +217,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     for (int y = 0; y < H; ++y) g.rows[y * g.stride] = rec[kRecHead + y];
   } else {
     // ---- committed state
-    const uint32_t* rows_c = p.rows + (size_t)cidx * H * nr;
+    const uint32_t* rows_c = p.rows + (size_t)cidx * HL * nr;
     for (int y = 0; y < H; ++y) g.rows[y * g.stride] = rows_c[(size_t)y * nr + r];
     g.hN = p.halo[0 * nr + r];
     g.hS = p.halo[1 * nr + r];
@@ -339,7 +342,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   }
 
   // times are >= 0, so their bit patterns order like their values
-  double tau = tau_any<SOFT>(tl, x, b, lam, p);
+  double tau = tau_any<SOFT>(tl, x, b, lam, lt);
   for (;;) {
     long long tbb;
     int db;
@@ -523,7 +526,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       }
     } else {
       // ---- break point: a neighbour flip at tb < tau (§5, Eqs. 5.2-5.6)
-      b = accrue_any<SOFT>(b, tb, tl, lam, p);
+      b = accrue_any<SOFT>(b, tb, tl, lam, lt);
       tl = tb;
       const unsigned pos = bpos;
       int ux, uy, up_now;
@@ -574,7 +577,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
       advance(db);
       ++brk;
     }
-    tau = tau_any<SOFT>(tl, x, b, lam, p);
+    tau = tau_any<SOFT>(tl, x, b, lam, lt);
   }
 
 #pragma unroll
@@ -591,7 +594,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   }
   // ---- tentative end state
   const unsigned tc = cidx ^ 1u;
-  uint32_t* rows_t = p.rows + (size_t)tc * H * nr;
+  uint32_t* rows_t = p.rows + (size_t)tc * HL * nr;
   for (int y = 0; y < H; ++y) rows_t[(size_t)y * nr + r] = g.row(y);
   p.ci[tc * nr + r] = i;
   p.cx[tc * nr + r] = x;
@@ -665,7 +668,7 @@ __device__ __forceinline__ long long shfl_xor_s64(long long v, int m) {
 __device__ void run_region_warp(const KParams& p, const Lat& lt, int r, int n_iter, unsigned cidx,
                                 double t_s, double t_end, Acc& acc) {
   const int lane = threadIdx.x & 31;
-  const int W = p.W, H = p.H;
+  const int W = lt.W, H = lt.H, HL = p.H;
   const size_t nr = (size_t)p.NR;
   const size_t cap = (size_t)p.cap;
   const int wp = n_iter & 1, rp = wp ^ 1;
@@ -709,7 +712,7 @@ __device__ void run_region_warp(const KParams& p, const Lat& lt, int r, int n_it
   if (lane == 0) acc.passes += 1;
 
   // ---- committed state
-  uint32_t row = vlane ? __ldcg(&p.rows[((size_t)cidx * H + lane) * nr + r]) : 0u;
+  uint32_t row = vlane ? __ldcg(&p.rows[((size_t)cidx * HL + lane) * nr + r]) : 0u;
   uint32_t hN = __ldcg(&p.halo[0 * nr + r]), hS = __ldcg(&p.halo[1 * nr + r]);
   uint32_t hW = __ldcg(&p.halo[2 * nr + r]), hE = __ldcg(&p.halo[3 * nr + r]);
   unsigned long long i = __ldcg(&p.ci[cidx * nr + r]);
@@ -727,7 +730,7 @@ __device__ void run_region_warp(const KParams& p, const Lat& lt, int r, int n_it
     px = __ldcg(&p.rx[a]);
     pkv = __ldcg(&p.rkv[a]);
   }
-  const int F = p.F;
+  const int F = lt.F;
 
   // neighbour words and per-position up counts of my row
   uint32_t s0, s1, s2;
@@ -1031,7 +1034,7 @@ __device__ void run_region_warp(const KParams& p, const Lat& lt, int r, int n_it
 
   // ---- tentative end state
   const unsigned tc = cidx ^ 1u;
-  if (vlane) p.rows[((size_t)tc * H + lane) * nr + r] = row;
+  if (vlane) p.rows[((size_t)tc * HL + lane) * nr + r] = row;
   if (lane == 0) {
     p.ci[tc * nr + r] = i;
     p.cx[tc * nr + r] = x;
@@ -1064,14 +1067,14 @@ __device__ void compute_halo(const KParams& p, const Lat& lt, int r, unsigned ci
   if (!lt.spans_y) {
     const int qN = lt.off + ((ry + lt.NY - 1) % lt.NY) * lt.NX + rx;
     const int qS = lt.off + ((ry + 1) % lt.NY) * lt.NX + rx;
-    hN = __ldcg(&rows_c[(size_t)(p.H - 1) * nr + qN]);
+    hN = __ldcg(&rows_c[(size_t)(lt.H - 1) * nr + qN]);
     hS = __ldcg(&rows_c[qS]);
   }
   if (!lt.spans_x) {
     const int qW = lt.off + ry * lt.NX + (rx + lt.NX - 1) % lt.NX;
     const int qE = lt.off + ry * lt.NX + (rx + 1) % lt.NX;
-    for (int y = 0; y < p.H; ++y) {
-      hW |= ((__ldcg(&rows_c[(size_t)y * nr + qW]) >> (p.W - 1)) & 1u) << y;
+    for (int y = 0; y < lt.H; ++y) {
+      hW |= ((__ldcg(&rows_c[(size_t)y * nr + qW]) >> (lt.W - 1)) & 1u) << y;
       hE |= (__ldcg(&rows_c[(size_t)y * nr + qE]) & 1u) << y;
     }
   }

@@ -33,10 +33,19 @@ struct DevStats {
 
 constexpr int kWinRing = 4096;
 
-// One lattice of a batch.  Every lattice of a launch shares the region shape;
-// its regions are numbered off .. off + NR - 1 in the global region index.
+// Task items of the asynchronous schedule: bit 63 valid, bit 62 kind,
+// bits 42-61 lattice, bits 20-41 chunk, bits 0-19 the tag of its ticket.
+constexpr unsigned long long kTaskValid = 1ull << 63;
+constexpr unsigned long long kTaskTag = (1ull << 20) - 1ull;
+constexpr int kTaskMaxLattices = 1 << 20;
+constexpr long long kTaskMaxChunks = 1ll << 22;
+
+// One lattice of a batch, with its own region shape; its regions are numbered
+// off .. off + NR - 1 in the global region index.
 struct RepDesc {
   int L, NX, NY, NR;            // side, regions across, regions down, regions
+  int W, H;                     // region shape (at most the launch's W, H)
+  int F;                        // rate grid 2^-F of this shape (63 - bitlen(W H))
   int off;                      // global index of its first region
   int spans_x, spans_y;         // a region covers the whole periodic extent
   uint32_t key0, key1;          // seed
@@ -44,6 +53,7 @@ struct RepDesc {
   int init_mode;                // SR_INIT_* of sr_reset
   unsigned w0;                  // windows committed before the current launch
   double t0, Tw;                // committed time at the launch, window length
+  double scale;                 // 2^-F
   unsigned long long P[10];     // p_k on the 2^-F grid
   unsigned long long Rp[10];    // floor((2^64 - 1) / P[k]) (0 when P[k] = 0)
 };
@@ -68,7 +78,8 @@ struct LatState {
 };
 
 struct KParams {
-  int W, H, NR;                 // region shape, regions of all lattices
+  int W, H, NR;                 // the largest region shape of any lattice (the layout of the
+                                // per-region arrays and of shared memory), regions of all lattices
   int nrep;                     // lattices
   const RepDesc* reps;
   const uint32_t* rrep;         // [NR] lattice of each region
@@ -80,8 +91,6 @@ struct KParams {
   uint32_t* rwin;               // [NR] windows the region committed in this launch
   double* rts;                  // [NR] start of the region's current window
   uint8_t* rfill;               // [NR] ring top-up pending
-  double scale;                 // 2^-F
-  int F;
   uint32_t* rows;               // [2][H][NR]   spin rows, bit x = site x of the row
   uint32_t* halo;               // [4][NR]      N, S, W, E halo words at t_c
   unsigned long long* ci;       // [2][NR]      index of the pending event
@@ -131,6 +140,8 @@ struct Lat {
   const unsigned long long* P;
   const unsigned long long* Rp;
   int L, NX, NY, off, loc, rep;
+  int W, H, F;                  // its region shape and rate grid
+  double scale;
   bool spans_x, spans_y;
   uint32_t key0, key1;
 };
@@ -145,6 +156,10 @@ __device__ __forceinline__ Lat lat_of(const KParams& p, int r) {
   t.NY = d->NY;
   t.off = d->off;
   t.loc = r - d->off;
+  t.W = d->W;
+  t.H = d->H;
+  t.F = d->F;
+  t.scale = d->scale;
   t.spans_x = d->spans_x != 0;
   t.spans_y = d->spans_y != 0;
   t.key0 = d->key0;
@@ -211,6 +226,13 @@ struct Region {
   uint32_t hN, hS, hW, hE;
 
   __device__ __forceinline__ uint32_t row(int y) const { return rows[y * stride]; }
+  // The region shape of the lattice being run (the layout is the launch's largest).
+  __device__ __forceinline__ void set_shape(int w, int h) {
+    W = w;
+    H = h;
+    hq = (h + 3) / 4;
+    wmask = (w == 32) ? 0xFFFFFFFFu : ((1u << w) - 1u);
+  }
   __device__ __forceinline__ unsigned long long P(int k) const { return PT[k * stride]; }
   __device__ __forceinline__ unsigned long long Rp(int k) const { return PT[(10 + k) * stride]; }
 

@@ -190,20 +190,72 @@ def test_adaptive_argument_checks():
             batch.run_adaptive([2.0, 2.0], tw_min=1.0, tw_max=0.5)
 
 
+MIXED = [dict(L=32, T=2.8, h=0.05, seed=81, region=(8, 8)),
+         dict(L=64, T=1.5, h=0.0, seed=82, region=(32, 16)),
+         dict(L=48, T=3.3, h=-0.1, seed=83, region=(16, 8), init="up"),
+         dict(L=64, T=2.2, h=0.1, seed=84),                       # the batch's shape
+         dict(L=32, T=1.2, h=0.2, seed=85, region=(32, 32), rates="glauber"),
+         dict(L=24, T=2.5, h=0.0, seed=86, region=(8, 12))]
+MIXED_TW = [0.5, 0.25, 0.5, 1.0, 0.5, 0.25]
+MIXED_NW = [4, 6, 3, 2, 4, 8]
+
+
+@pytest.mark.parametrize("m", range(len(MAPS)))
+def test_lattices_with_their_own_region_shapes(m):
+    """Each lattice of a batch partitioned into its own region shape (§5: the
+    subsets G_i); the launch lays its state out for the largest shape.  Every
+    lattice against the oracle with that lattice's shape, in every mapping
+    and schedule."""
+    with sr.Batch(MIXED, region=(16, 16), **MAPS[m]) as batch:
+        batch.run(MIXED_TW, MIXED_NW)
+        for b in range(len(MIXED)):
+            W, H = batch.region_of(b)
+            assert (W, H) == MIXED[b].get("region", (16, 16))
+            _check_lattice(batch, b, W, H, MIXED_TW[b], MIXED_NW[b])
+
+
+def test_own_region_shapes_checkpoint_and_score():
+    reps = [dict(r) for r in MIXED[:4]]
+    with sr.Batch(reps, region=(16, 16), score=True) as a:
+        a.run(MIXED_TW[:4], [2, 3, 2, 1])
+        data = a.checkpoint()
+        a.run(MIXED_TW[:4], [2, 3, 1, 1])
+        S_a = a.score()
+        spins_a = [a.spins(b) for b in range(4)]
+    with sr.Batch(reps, region=(16, 16), score=True) as b2:
+        b2.load_checkpoint(data)
+        b2.run(MIXED_TW[:4], [2, 3, 1, 1])
+        assert np.array_equal(b2.score(), S_a)
+        for b in range(4):
+            assert np.array_equal(b2.spins(b), spins_a[b])
+    other = [dict(r) for r in reps]
+    other[1]["region"] = (16, 16)            # a different shape: the checkpoint does not fit
+    with sr.Batch(other, region=(16, 16), score=True) as b3:
+        with pytest.raises(sr.SRError):
+            b3.load_checkpoint(data)
+
+
 def test_autotune_small_batch():
     reps = [dict(L=32, T=1.5, h=0.05, seed=31), dict(L=64, T=3.0, h=0.0, seed=32),
             dict(L=96, T=2.2, h=-0.1, seed=33)]
     t = sr.autotune(reps, t_trial=0.5)
     # 96 is not a multiple of 64 but every candidate shape divides 32, 64, 96
-    assert (t.region[0], t.region[1]) in [(16, 16), (8, 8), (32, 32), (16, 8), (32, 16)]
+    shapes = [(16, 16), (8, 8), (32, 32), (16, 8), (32, 16)]
+    assert (t.region[0], t.region[1]) in shapes and t.region == t.shapes[0]
+    assert all(s in shapes for s in t.shapes) and len(t.shapes) == 3
+    assert t.rate_threshold in (0.0, 32.0, 64.0, 128.0, 256.0)
+    if t.rate_threshold == 0.0:
+        assert len(set(t.shapes)) == 1          # one common shape won
     assert t.lanes_per_warp in (0, 8, 16, 32)
     assert t.kappa in (4.0, 8.0, 16.0, 32.0)
-    assert t.trials == 5 + 3 + 3
+    assert t.trials == 5 + 4 + 3 + 3
     assert t.flips_per_s > 0
-    with sr.Batch(reps, region=t.region, lanes_per_warp=t.lanes_per_warp) as batch:
+    with sr.Batch(t.replicas(reps), region=t.region, lanes_per_warp=t.lanes_per_warp) as batch:
         batch.run_adaptive(1.0, kappa=t.kappa)
         for b in range(3):
-            _check_at(batch, b, t.region[0], t.region[1], 1.0)
+            W, H = batch.region_of(b)
+            assert (W, H) == t.shapes[b]
+            _check_at(batch, b, W, H, 1.0)
     with pytest.raises(sr.SRError):
         sr.autotune([dict(L=36, T=2.0)])              # no candidate shape divides 36
 
@@ -223,7 +275,7 @@ def test_batched_workload_sample_bit_exact():
 
 def test_benched_batch_configuration_against_the_oracle():
     """The batched workload exactly as the benchmark runs it: the autotuner's
-    region shape, lanes per warp and kappa, the automatic (asynchronous)
+    region shape of each lattice, lanes per warp and kappa, the automatic (asynchronous)
     schedule, adaptive window lengths, a warm-up run and a reset, then every
     lattice to t = 10.  A stratified sample of 15 lattices (the coldest, the
     median and the hottest of each side L) against their oracle runs: spins,
@@ -233,13 +285,14 @@ def test_benched_batch_configuration_against_the_oracle():
     sample = workloads.stratified(reps, per_side=3)
     assert len(sample) == 15
     tune = sr.autotune(reps, t_trial=1.0)
-    W, H = tune.region
     pool = oracle_pool.pool(len(sample))
     try:
         jobs = {b: pool.apply_async(oracle_pool.run, (dict(
-            L=reps[b]["L"], J=reps[b]["J"], h=reps[b]["h"], T=reps[b]["T"], region_w=W,
-            region_h=H, seed=reps[b]["seed"], t_end=[10.0]),)) for b in sample}
-        with sr.Batch(reps, region=tune.region, lanes_per_warp=tune.lanes_per_warp) as bt:
+            L=reps[b]["L"], J=reps[b]["J"], h=reps[b]["h"], T=reps[b]["T"],
+            region_w=tune.shapes[b][0], region_h=tune.shapes[b][1], seed=reps[b]["seed"],
+            t_end=[10.0]),)) for b in sample}
+        with sr.Batch(tune.replicas(reps), region=tune.region,
+                      lanes_per_warp=tune.lanes_per_warp) as bt:
             bt.run_adaptive(1.0, kappa=tune.kappa)
             bt.reset()
             bt.run_adaptive(10.0, kappa=tune.kappa)
@@ -258,6 +311,35 @@ def test_benched_batch_configuration_against_the_oracle():
     finally:
         pool.terminate()
         pool.join()
+
+
+def test_many_short_asynchronous_launches_from_coarsened_spins():
+    """The task queue of the asynchronous schedule under many short launches:
+    the 256-lattice workload with a region shape per lattice, restarted 30
+    times from coarsened spins (the state at t = 4) and run to t = 1 in
+    chunks of 1/4.  Every launch must end normally (a lost or repeated task
+    would leave a lattice waiting until the bounded wait ends it with
+    SR_TIMEOUT), and the last run of three lattices equals the oracle from
+    the same spins."""
+    from paper_cs_0405053_gb300 import workloads
+    reps = workloads.batch_replicas()
+    shapes = [(8, 8), (16, 8), (16, 16), (32, 16)]
+    own = [dict(r, region=shapes[b % 4]) for b, r in enumerate(reps)]
+    with sr.Batch(own, region=(16, 16)) as bt:
+        bt.run_adaptive(4.0, kappa=8.0)
+        late = [bt.spins(b) for b in range(len(reps))]
+        for _ in range(30):
+            for b in range(len(reps)):
+                bt.set_spins(b, late[b])
+            bt.run_adaptive(1.0, kappa=4.0, chunk=0.25)
+            assert np.all(bt.t_c == 1.0)
+        for b in (0, 101, 255):
+            W, H = shapes[b % 4]
+            r = reps[b]
+            ref = oracle.run(r["L"], r["J"], r["h"], r["T"], W, H, r["seed"], [1.0],
+                             init_spins=late[b])
+            assert np.array_equal(bt.spins(b), ref.spins[-1]), b
+            assert np.array_equal(bt.carry(b)[0], ref.carry_i), b
 
 
 # ----------------------------------------------------------------- errors in a batch
