@@ -243,14 +243,15 @@ int sr_run_batch_adaptive(sr_ctx* ctx, const double* t_end, const sr_adapt* opts
 
 /* ---- autotuner ----
  * Chooses, for a batch of lattices, the region shape of every lattice, the
- * region lanes per warp (automatic, 8, 16, 32) and kappa (4, 8, 16, 32) by
+ * region lanes per warp (automatic, 8, 16, 32) and kappa (4, 8, 11.3, 16) by
  * timing trial runs of the real lattices.  A warm-up run (the first of the
  * shapes below that divides every L, to t = 8 t_trial) measures each
  * lattice's committed events per site per unit time rho_b over its second
  * half and keeps the spins it ends with; every trial starts from those
  * spins (the coarsened configurations of a long run, not the first quench
- * from the initial spins), runs the adaptive runner untimed to t_trial / 2,
- * then timed to t_trial, and scores committed flips per second.  One
+ * from the initial spins), runs the adaptive runner with one launch per
+ * t_trial, untimed to t_trial (the window lengths settle), then timed to
+ * 3 t_trial, and scores committed flips per second.  One
  * coordinate at a time:
  *   1. one shape for every lattice, among 8x8, 16x8, 16x16, 32x16 and 32x32;
  *   2. a shape per lattice: the largest of those shapes (dividing L_b) with

@@ -137,12 +137,21 @@ __device__ __forceinline__ unsigned long long poll_slot(unsigned long long* a) {
 __device__ __forceinline__ unsigned long long poll_word(const unsigned long long* a) { return __ldcg(a); }
 __device__ __forceinline__ unsigned poll_word(const unsigned* a) { return __ldcg(a); }
 
-__device__ void enqueue_lattice(const KParams& p, int b, unsigned kind, int chunk) {
+// The task set of lattice b (one task per chunk of `chunk` regions), published
+// by all 32 lanes of the calling warp: lane 0 reserves the tickets, lane j
+// writes the items of chunks j, j + 32, ...  An item goes into an empty slot
+// only (compare-and-swap), waiting within the bounded wait for an older item
+// still there to be taken.  One lane writing every item in turn kept the last
+// task of a large lattice waiting for dozens of round trips to L2.
+__device__ void enqueue_lattice(const KParams& p, int b, unsigned kind, int chunk, int lane) {
   const int nreg = p.reps[b].NR;
   const unsigned long long nch = (unsigned long long)((nreg + chunk - 1) / chunk);
-  __threadfence();
-  const unsigned long long base = atomicAdd(&p.st->qtail, nch);
-  for (unsigned long long c = 0; c < nch; ++c) {
+  unsigned long long base = 0ull;
+  if (lane == 0) base = atomicAdd(&p.st->qtail, nch);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  __syncwarp();
+  __threadfence();     // the lattice state lane 0 wrote comes before every item
+  for (unsigned long long c = (unsigned long long)lane; c < nch; c += 32ull) {
     const unsigned long long t = base + c;
     const unsigned long long item = task_item(kind, (unsigned)b, (unsigned)c, t);
     unsigned long long* slot = &p.q[t % p.qcap];
@@ -327,12 +336,15 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
         fill_warp<GEN>(p, mine && w + 1u < (unsigned)d->nwin, r, (uint32_t)loc, d->key0, d->key1,
                        d->w0 + w + 1u);
         __syncwarp();        // every lane's writes come before lane 0's release
+        int enq = -1;        // task kind the warp publishes next (-1: none)
+        bool last = false;   // this task completed the window's commit
+        const unsigned wn = w + 1u;
         if (lane == 0) {
           __threadfence();
           const unsigned old = atomicSub(&Ls->pend, cnt);
           if (old == cnt) {
             __threadfence();
-            const unsigned wn = w + 1u;
+            last = true;
             const unsigned n = poll_word(&Ls->n);      // iterations of window w
             rs->windows += 1ull;
             rs->iterations += (unsigned long long)n;
@@ -354,8 +366,14 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
               atomicExch(&Ls->pend, (unsigned)d->NR);
               atomicExch((unsigned long long*)&Ls->ts, (unsigned long long)__double_as_longlong(
                   __dadd_rn(__ldcg(&Ls->ts), d->Tw)));
-              enqueue_lattice(p, b, 0u, CH);
+              enq = 0;
             }
+          }
+        }
+        enq = __shfl_sync(0xFFFFFFFFu, enq, 0);
+        if (enq >= 0) enqueue_lattice(p, b, (unsigned)enq, CH, lane);
+        if (lane == 0) {
+          if (last) {
             __threadfence();
             if (wn == (unsigned)d->nwin) atomicSub(&st->active, 1u);
           }
@@ -363,7 +381,8 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
         }
       } else {
         // ---- iteration n of window w; after an error no new passes run
-        if (poll_word(&st->status) & kStop) continue;
+        // (one lane's read decides for the warp: the reductions below need every lane)
+        if (__shfl_sync(0xFFFFFFFFu, poll_word(&st->status), 0) & kStop) continue;
         const unsigned n = poll_word(&Ls->n);
         const double t_s = __ldcg(&Ls->ts);
         const double t_end = __dadd_rn(t_s, d->Tw);
@@ -375,18 +394,26 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
             run_region<1, GEN>(p, lt, r, (int)n, cidx, t_s, t_end, d->w0 + w, g, ra);
           else
             run_region<0, GEN>(p, lt, r, (int)n, cidx, t_s, t_end, d->w0 + w, g, ra);
-          if (ra.fmax) atomicMax(&p.curf[(w & 1u) * p.nrep + b], ra.fmax);
-          if (ra.events) atomicAdd(&rs->generated, (unsigned long long)ra.events);
-          if (ra.breaks) atomicAdd(&rs->breaks, (unsigned long long)ra.breaks);
-          if (ra.fmax) atomicMax(&rs->max_f, ra.fmax);
-          if (ra.emax) atomicMax(&rs->max_win_events, ra.emax);
-          if (ra.passes) atomicAdd(&st->region_passes, (unsigned long long)ra.passes);
-          if (ra.skips) atomicAdd(&st->region_skips, (unsigned long long)ra.skips);
         }
+        // the task's counters, reduced over the warp: one atomic per counter
+        const unsigned t_ev = __reduce_add_sync(0xFFFFFFFFu, ra.events);
+        const unsigned t_br = __reduce_add_sync(0xFFFFFFFFu, ra.breaks);
+        const unsigned t_pa = __reduce_add_sync(0xFFFFFFFFu, ra.passes);
+        const unsigned t_sk = __reduce_add_sync(0xFFFFFFFFu, ra.skips);
+        const unsigned t_fm = __reduce_max_sync(0xFFFFFFFFu, ra.fmax);
+        const unsigned t_em = __reduce_max_sync(0xFFFFFFFFu, ra.emax);
         const bool anych = __any_sync(0xFFFFFFFFu, mine && ra.changed);
         const bool anyov = __any_sync(0xFFFFFFFFu, mine && ra.overflow);
         __syncwarp();        // every lane's writes come before lane 0's release
+        int enq = -1;        // task kind the warp publishes next (-1: none)
         if (lane == 0) {
+          if (t_fm) atomicMax(&p.curf[(w & 1u) * p.nrep + b], t_fm);
+          if (t_ev) atomicAdd(&rs->generated, (unsigned long long)t_ev);
+          if (t_br) atomicAdd(&rs->breaks, (unsigned long long)t_br);
+          if (t_fm) atomicMax(&rs->max_f, t_fm);
+          if (t_em) atomicMax(&rs->max_win_events, t_em);
+          if (t_pa) atomicAdd(&st->region_passes, (unsigned long long)t_pa);
+          if (t_sk) atomicAdd(&st->region_skips, (unsigned long long)t_sk);
           if (anych) atomicOr(&Ls->chg, 1u);
           if (anyov) atomicOr(&Ls->ovf, 1u);
           __threadfence();
@@ -405,17 +432,19 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
               if (before & kCworkStop)
                 atomicAdd(&st->cwork, 0ull - (unsigned long long)d->NR);   // stopped: no commit
               else
-                enqueue_lattice(p, b, 1u, CH);
+                enq = 1;
             } else if ((int)n >= p.max_iters) {
               stop_all(ST_NOT_CONVERGED);
             } else if (!(poll_word(&st->status) & kStop)) {
               atomicExch(&Ls->n, n + 1u);
               atomicExch(&Ls->chg, 0u);
               atomicExch(&Ls->pend, (unsigned)d->NR);
-              enqueue_lattice(p, b, 0u, CH);
+              enq = 0;
             }
           }
         }
+        enq = __shfl_sync(0xFFFFFFFFu, enq, 0);
+        if (enq >= 0) enqueue_lattice(p, b, (unsigned)enq, CH, lane);
       }
     }
     return;

@@ -1416,8 +1416,10 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
     p.lanes_per_warp = lpw;
     return create_common(c, rr.data(), n, p);
   };
-  // one trial of a shape assignment from the warm-up run's spins: committed
-  // flips per second over [t_trial / 2, t_trial]
+  // one trial of a shape assignment from the warm-up run's spins, with the
+  // launch length of the default adaptive run (one launch per t_trial): the
+  // first launch settles the window lengths, committed flips per second over
+  // the next two are the score
   auto trial = [&](int lpw, double kappa, double* score) -> int {
     sr_ctx* c = nullptr;
     int rc = make(lpw, &c);
@@ -1427,13 +1429,13 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
     sr_adapt o;
     std::memset(&o, 0, sizeof o);
     o.kappa = kappa;
-    o.chunk = t_trial / 4.0;
-    for (int b = 0; b < n; ++b) te[(size_t)b] = 0.5 * t_trial;
+    o.chunk = t_trial;
+    for (int b = 0; b < n; ++b) te[(size_t)b] = t_trial;
     if (rc == SR_OK) rc = sr_run_batch_adaptive(c, te.data(), &o, nullptr);
     unsigned long long before = 0, after = 0;
     for (int b = 0; b < n && rc == SR_OK; ++b) before += c->h_rs[b].committed;
     const auto t0 = std::chrono::steady_clock::now();
-    for (int b = 0; b < n; ++b) te[(size_t)b] = t_trial;
+    for (int b = 0; b < n; ++b) te[(size_t)b] = 3.0 * t_trial;
     if (rc == SR_OK) rc = sr_run_batch_adaptive(c, te.data(), &o, nullptr);
     const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (int b = 0; b < n && rc == SR_OK; ++b) after += c->h_rs[b].committed;
@@ -1517,7 +1519,7 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
     if (rc == SR_OK && keep(sc)) bthr = thresholds[i];
   }
   // 3. kappa, then 4. region lanes per warp, with the best assignment
-  const double kappas[3] = {4.0, 16.0, 32.0};
+  const double kappas[3] = {4.0, 11.3137, 16.0};
   for (int i = 0; i < 3 && rc == SR_OK; ++i) {
     sw = best_w;
     sh = best_h;
