@@ -750,6 +750,15 @@ def run_grad(args):
         fwd_s = time.perf_counter() - w0
         row = {"T": T, "h": h, "init": spec.init, "forward_s": round(fwd_s, 3)}
         fd_dmdh = None
+        # the common-random-number runs at theta +- Delta e_q, shared by both outputs
+        sims = []
+        for q in range(3):
+            tp, tm = theta.detach().clone(), theta.detach().clone()
+            tp[:, q] += 1e-3
+            tm[:, q] -= 1e-3
+            sims.append((grad._simulate(tp.cpu().numpy(), spec)[0],
+                         grad._simulate(tm.cpu().numpy(), spec)[0]))
+        row["fd_s"] = round(time.perf_counter() - w0 - fwd_s, 3)
         for j, name in enumerate(("m", "e")):
             theta.grad = None
             A[:, j].sum().backward(retain_graph=True)
@@ -757,11 +766,7 @@ def run_grad(args):
             est, se = g.mean(axis=0), g.std(axis=0, ddof=1) / math.sqrt(R)
             fds, fdse = [], []
             for q in range(3):
-                tp, tm = theta.detach().clone(), theta.detach().clone()
-                tp[:, q] += 1e-3
-                tm[:, q] -= 1e-3
-                ap = grad._simulate(tp.cpu().numpy(), spec)[0][:, j]
-                am = grad._simulate(tm.cpu().numpy(), spec)[0][:, j]
+                ap, am = sims[q][0][:, j], sims[q][1][:, j]
                 fd = (ap - am) / 2e-3
                 if (j, q) == (0, 1):
                     fd_dmdh = fd

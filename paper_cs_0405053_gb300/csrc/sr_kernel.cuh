@@ -203,9 +203,21 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
   g.rows = smem + (LANES && is_slot ? slot : 0);
   g.C = smem + p.H * stride + (LANES && is_slot ? slot : 0);
   {
-    const int pt_words = ((p.H + 10 * g.hq) * stride + 1) & ~1;   // 8-byte aligned table
-    g.PT = reinterpret_cast<unsigned long long*>(smem + pt_words) + (LANES && is_slot ? slot : 0);
-    g.SX = g.PT + 20 * stride;                                       // score mode only
+    const int pt_words = ((p.H + 10 * g.hq) * stride + 1) & ~1;   // 8-byte aligned tables
+    unsigned long long* tab = reinterpret_cast<unsigned long long*>(smem + pt_words);
+    if (DYN == 2 && LANES) {
+      // asynchronous schedule: the lanes of a warp all run one lattice's task,
+      // so they share one rate table (a lane reading P_k and one reading P_k'
+      // touch different banks; equal k is a broadcast) -- 160 bytes of shared
+      // memory per region slot less, so more blocks fit on an SM
+      g.PT = tab + 20 * warp;
+      g.pts = 1;
+      g.SX = tab + 20 * (int)(blockDim.x >> 5) + (is_slot ? slot : 0);   // score mode only
+    } else {
+      g.PT = tab + (LANES && is_slot ? slot : 0);
+      g.pts = stride;
+      g.SX = g.PT + 20 * stride;                                       // score mode only
+    }
   }
   g.cur_rep = -1;
   g.stride = stride;
@@ -273,6 +285,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
       atomicOr(&st->cwork, kCworkStop);
     };
     const int CH = p.lanes;
+    int warp_rep = -1;       // lattice whose rates the warp's table holds
     for (;;) {
       unsigned long long item = 0ull;
       if (lane == 0) {
@@ -316,6 +329,17 @@ __global__ void __launch_bounds__(MODE == 1 ? 128 : SR_LANE_MAX_THREADS,
       const int c = (int)((item >> 20) & 0x3FFFFFull);
       const RepDesc* d = p.reps + b;
       LatState* Ls = p.ls + b;
+      if (kind == 0u && warp_rep != b) {
+        // the warp's rate table for this lattice (every lane has finished
+        // with the last one: the item's shuffle above synchronised the warp)
+        if (lane < 10) {
+          g.PT[lane] = d->P[lane];
+          g.PT[10 + lane] = d->Rp[lane];
+        }
+        __syncwarp();
+        warp_rep = b;
+      }
+      g.cur_rep = warp_rep;
       const int loc = c * CH + lane;
       const bool mine = is_slot && lane < CH && loc < d->NR;
       const int r = d->off + loc;

@@ -180,8 +180,8 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   if (g.cur_rep != lt.rep) {
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
-      g.PT[k * g.stride] = lt.P[k];
-      g.PT[(10 + k) * g.stride] = lt.Rp[k];
+      g.PT[k * g.pts] = lt.P[k];
+      g.PT[(10 + k) * g.pts] = lt.Rp[k];
     }
     g.cur_rep = lt.rep;
   }
@@ -214,11 +214,11 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
     g.hS = rec[21];
     g.hW = rec[22];
     g.hE = rec[23];
-    for (int y = 0; y < H; ++y) g.rows[y * g.stride] = rec[kRecHead + y];
+    for (int y = 0; y < H; ++y) cp_async4(&g.rows[y * g.stride], &rec[kRecHead + y]);
   } else {
     // ---- committed state
     const uint32_t* rows_c = p.rows + (size_t)cidx * HL * nr;
-    for (int y = 0; y < H; ++y) g.rows[y * g.stride] = rows_c[(size_t)y * nr + r];
+    for (int y = 0; y < H; ++y) cp_async4(&g.rows[y * g.stride], &rows_c[(size_t)y * nr + r]);
     g.hN = p.halo[0 * nr + r];
     g.hS = p.halo[1 * nr + r];
     g.hW = p.halo[2 * nr + r];
@@ -267,6 +267,7 @@ __device__ void run_region(const KParams& p, const Lat& lt, int r, int n_iter, u
   Counts N;
   int mag0 = 0, bond0 = 0;
   uint32_t cw[10];
+  cp_async_wait_all();               // the rows copied above
 #pragma unroll
   for (int k = 0; k < 10; ++k) cw[k] = 0;
   for (int y = 0; y < H; ++y) {

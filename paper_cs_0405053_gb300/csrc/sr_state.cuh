@@ -212,12 +212,14 @@ __device__ __noinline__ bool grid_barrier(DevStats* st, long long timeout) {
 struct Region {
   uint32_t* rows;              // rows[y * stride]
   uint32_t* C;                 // C[(k * hq + y/4) * stride]: byte y%4 = sites of class k in row y
-  unsigned long long* PT;      // PT[k * stride] = P_k, PT[(10 + k) * stride] = its reciprocal
+  unsigned long long* PT;      // PT[k * pts] = P_k, PT[(10 + k) * pts] = its reciprocal
   // score mode: per class the window's event count SX[k * stride] and the
   // window's occupancy sum as a 128-bit fixed-point number,
   // SX[(10 + 2k) * stride] (low word) and SX[(11 + 2k) * stride] (high word)
   unsigned long long* SX;
   int cur_rep;                 // lattice whose table PT holds (-1: none)
+  int pts;                     // stride of PT: the slot stride (a table per region slot) or 1
+                               // (one table per warp, whose lanes all run one lattice)
   int hq;                      // count words per class, (H + 3) / 4
   int stride;
   int W, H;
@@ -233,8 +235,8 @@ struct Region {
     hq = (h + 3) / 4;
     wmask = (w == 32) ? 0xFFFFFFFFu : ((1u << w) - 1u);
   }
-  __device__ __forceinline__ unsigned long long P(int k) const { return PT[k * stride]; }
-  __device__ __forceinline__ unsigned long long Rp(int k) const { return PT[(10 + k) * stride]; }
+  __device__ __forceinline__ unsigned long long P(int k) const { return PT[k * pts]; }
+  __device__ __forceinline__ unsigned long long Rp(int k) const { return PT[(10 + k) * pts]; }
 
   // Row y for y in [-2, H + 1]: periodic inside a region spanning the lattice,
   // else the halo row for y = -1 and y = H (0 beyond, never used).
@@ -316,6 +318,16 @@ struct Counts {
     if (to < 5) lo += dt; else hi += dt;
   }
 };
+
+// A 4-byte asynchronous copy from global to shared memory (cp.async): the
+// copies of a loop are in flight together.
+__device__ __forceinline__ void cp_async4(uint32_t* dst_shared, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::
+               "r"((unsigned)__cvta_generic_to_shared(dst_shared)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 // Per-position sum of four bits as a 3-bit number (b0, b1, b2).
 __device__ __forceinline__ void add4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t& s0,
