@@ -215,6 +215,31 @@ int sr_create_batch(sr_ctx** out, const sr_replica* reps, int n, const sr_params
  * its last converged window. */
 int sr_run_batch(sr_ctx* ctx, const double* Tw, const int* n_windows);
 
+/* ---- relaxation launches replayed from a CUDA graph ----
+ * One launch is the whole procedure of §4 for the launch's windows (passes,
+ * the fixed-point test, commits); the graph form has no counterpart in the
+ * paper.  on != 0: every later relaxation launch of this context (those of
+ * sr_run_window(s), sr_run_batch and sr_run_batch_adaptive) runs as one CUDA
+ * graph -- the uploads of the launch plan, the resets of the launch state,
+ * the persistent kernel as a cooperative kernel node and the read-back of
+ * the status -- launched on the context's stream.  The graph is captured (on
+ * a stream of its own) at the first launch and replayed while the kernel's
+ * parameters and the number of first tasks stay the same; the plan's values
+ * (committed times, window lengths and counts, first tasks) are staged in
+ * pinned host memory that the graph's copies read each time it runs.  A new
+ * ring length or history capacity recaptures it.  Trajectories, counts and
+ * observables are those of launches without the graph, bit for bit;
+ * sr_obs.relax_ms then times whole graphs (uploads and read-back included).
+ * The call synchronises the context's stream; on == 0 frees the graph and
+ * its staging.  Errors: SR_EINVAL (ctx NULL), SR_ENOMEM (pinned staging),
+ * SR_ECUDA; a later launch returns SR_EUNSUPPORTED if the capture or the
+ * instantiation is refused. */
+int sr_set_graph_launch(sr_ctx* ctx, int on);
+
+/* Graph captures and graph launches of this context so far (either pointer
+ * may be NULL).  Errors: SR_EINVAL (ctx NULL). */
+int sr_get_graph_stats(sr_ctx* ctx, unsigned long long* captures, unsigned long long* replays);
+
 /* ---- window lengths matched to event rates ----
  * The paper leaves T_max free (§4, §6: the cost per step grows with the
  * boundary events f per region and the iterations g).  Window ends are not

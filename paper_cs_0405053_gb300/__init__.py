@@ -155,6 +155,8 @@ def library(build_if_missing: bool = True) -> C.CDLL:
             "sr_strerror": (C.c_char_p, [C.c_int]),
             "sr_create_batch": (C.c_int, [C.POINTER(_P), _P, C.c_int, C.POINTER(_Params)]),
             "sr_run_batch": (C.c_int, [_P, _P, _P]),
+            "sr_set_graph_launch": (C.c_int, [_P, C.c_int]),
+            "sr_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
             "sr_observables_replica": (C.c_int, [_P, C.c_int, C.POINTER(_Obs)]),
             "sr_get_spins_replica": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
             "sr_set_spins_replica": (C.c_int, [_P, C.c_int, _P, C.c_size_t]),
@@ -192,6 +194,16 @@ def _checkpoint(ctx) -> bytes:
 def _load_checkpoint(ctx, data: bytes) -> None:
     data = bytes(data)
     _check(library().sr_checkpoint_load(ctx, data, len(data)), "sr_checkpoint_load")
+
+
+def _graph_launch(ctx, on: bool) -> None:
+    _check(library().sr_set_graph_launch(ctx, 1 if on else 0), "sr_set_graph_launch")
+
+
+def _graph_stats(ctx) -> Tuple[int, int]:
+    cap, rep = C.c_ulonglong(), C.c_ulonglong()
+    _check(library().sr_get_graph_stats(ctx, C.byref(cap), C.byref(rep)), "sr_get_graph_stats")
+    return cap.value, rep.value
 
 
 def _check(code: int, what: str) -> None:
@@ -333,6 +345,15 @@ class Lattice:
     def reset(self) -> None:
         _check(library().sr_reset(self._ctx), "sr_reset")
         self.t_c = 0.0
+
+    def graph_launch(self, on: bool = True) -> None:
+        """Run every later relaxation launch as a replayed CUDA graph (see
+        sr_set_graph_launch); off frees the graph."""
+        _graph_launch(self._ctx, on)
+
+    def graph_stats(self) -> Tuple[int, int]:
+        """(graph captures, graph launches) of this context."""
+        return _graph_stats(self._ctx)
 
     def checkpoint(self) -> bytes:
         """The committed state (spins, clock carry, integrals, counters) as
@@ -531,6 +552,15 @@ class Batch:
     def reset(self) -> None:
         _check(library().sr_reset(self._ctx), "sr_reset")
         self.t_c[:] = 0.0
+
+    def graph_launch(self, on: bool = True) -> None:
+        """Run every later relaxation launch as a replayed CUDA graph (see
+        sr_set_graph_launch); off frees the graph."""
+        _graph_launch(self._ctx, on)
+
+    def graph_stats(self) -> Tuple[int, int]:
+        """(graph captures, graph launches) of this context."""
+        return _graph_stats(self._ctx)
 
     def checkpoint(self) -> bytes:
         """The committed state of every lattice as bytes (see Lattice.checkpoint)."""

@@ -91,6 +91,21 @@ struct sr_ctx {
   cudaEvent_t ev_relax[2];
   double relax_ms;
   unsigned long long relax_launches;
+  // graph form of the relaxation launch (sr_set_graph_launch): the captured,
+  // instantiated launch, what it was captured with, and the pinned staging its
+  // copies read each time it runs
+  bool use_graph;
+  cudaStream_t gstream;         // capture stream (the context's may be the legacy stream)
+  cudaGraphExec_t gexec;
+  KParams gk;                   // kernel parameters of the captured launch
+  unsigned long long g_total;   // task items the captured launch uploads
+  RepDesc* p_desc;              // [nrep]
+  LatState* p_ls;               // [nrep]
+  unsigned long long* p_items;  // [p_items_cap]
+  unsigned long long p_items_cap;
+  unsigned long long* p_tail;   // [1] tasks published before the launch
+  unsigned* p_active;           // [1] lattices with windows
+  unsigned long long graph_captures, graph_launches;
 };
 
 namespace {
@@ -306,6 +321,179 @@ int init_state(sr_ctx* c, int rep, const int8_t* dev_spins) {
   return cuda_rc(cudaGetLastError());
 }
 
+// ---- the relaxation launch as a CUDA graph (sr_set_graph_launch)
+void free_graph(sr_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  void* pinned[] = {c->p_desc, c->p_ls, c->p_items, c->p_tail, c->p_active};
+  for (void* h : pinned)
+    if (h) cudaFreeHost(h);
+  c->gexec = nullptr;
+  c->gstream = nullptr;
+  c->p_desc = nullptr;
+  c->p_ls = nullptr;
+  c->p_items = nullptr;
+  c->p_items_cap = 0ull;
+  c->p_tail = nullptr;
+  c->p_active = nullptr;
+}
+
+// Capture the launch on the capture stream: the plan's uploads from the pinned
+// staging, the state resets, the persistent kernel as a cooperative kernel
+// node (its parameters k are copied into the node) and the read-back of the
+// status into pinned memory.  Instantiated into c->gexec.  (The timing events
+// are recorded around the graph's launch, not captured: event-record nodes of
+// a captured graph give no elapsed time.)
+int capture_launch(sr_ctx* c, const KParams& k, unsigned long long total) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  cudaStream_t s = c->gstream;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return SR_EUNSUPPORTED;
+  }
+  const size_t n = (size_t)c->nrep;
+  bool ok = cudaMemcpyAsync(c->desc, c->p_desc, n * sizeof(RepDesc), cudaMemcpyHostToDevice, s) ==
+            cudaSuccess;
+  if (c->dynamic == 2) {
+    ok = ok && cudaMemcpyAsync(c->ls, c->p_ls, n * sizeof(LatState), cudaMemcpyHostToDevice, s) ==
+                   cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->q, 0, (size_t)c->qcap * 8, s) == cudaSuccess;
+    if (total)
+      ok = ok && cudaMemcpyAsync(c->q, c->p_items, (size_t)total * 8, cudaMemcpyHostToDevice, s) ==
+                     cudaSuccess;
+  }
+  ok = ok && cudaMemsetAsync(c->st, 0, offsetof(DevStats, region_passes), s) == cudaSuccess &&
+       cudaMemsetAsync(c->rflags, 0, 3 * n * sizeof(uint32_t), s) == cudaSuccess &&
+       cudaMemsetAsync(c->curf, 0, 2 * n * sizeof(uint32_t), s) == cudaSuccess;
+  if (c->dynamic == 2)
+    ok = ok &&
+         cudaMemcpyAsync((char*)c->st + offsetof(DevStats, qtail), c->p_tail, 8,
+                         cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync((char*)c->st + offsetof(DevStats, active), c->p_active, 4,
+                         cudaMemcpyHostToDevice, s) == cudaSuccess;
+  if (ok) {
+    KParams kk = k;
+    void* args[] = {&kk};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(c->blocks);
+    cfg.blockDim = dim3(c->tpb);
+    cfg.dynamicSmemBytes = c->smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ok = cudaLaunchKernelExC(&cfg, relax_fn(c->mode, c->dynamic, gen_features(c->prm)), args) ==
+         cudaSuccess;
+  }
+  ok = ok &&
+       cudaMemcpyAsync(c->h_st, c->st, sizeof(DevStats), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+       cudaMemcpyAsync(c->h_rs, c->rs, n * sizeof(RepStats), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (!ok || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return SR_EUNSUPPORTED;
+  }
+  cudaGraphExec_t x = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return SR_EUNSUPPORTED;
+  }
+  c->gexec = x;
+  c->gk = k;
+  c->g_total = total;
+  c->graph_captures += 1;
+  return SR_OK;
+}
+
+// The launch of launch_relax, run from the graph: the plan is staged in pinned
+// memory, the graph recaptured when the kernel parameters or the number of
+// task items differ from the captured ones, then launched on the context's
+// stream.  Results are those of launch_relax bit for bit (same kernel, same
+// uploads).
+int launch_relax_graph(sr_ctx* c, const double* Tw, const int* nwin) {
+  for (int b = 0; b < c->nrep; ++b) {
+    c->hdesc[b].t0 = c->t_c[b];
+    c->hdesc[b].Tw = Tw[b];
+    c->hdesc[b].nwin = nwin[b];
+    c->hdesc[b].w0 = c->wins[b];
+  }
+  std::memcpy(c->p_desc, c->hdesc, (size_t)c->nrep * sizeof(RepDesc));
+  unsigned long long total = 0ull;
+  if (c->dynamic == 2) {
+    unsigned active = 0u;
+    for (int b = 0; b < c->nrep; ++b)
+      if (nwin[b] > 0) {
+        total += (unsigned long long)((c->hdesc[b].NR + c->lanes - 1) / c->lanes);
+        ++active;
+      }
+    if (total > c->p_items_cap) {
+      // a new staging buffer: the captured copy reads the old address
+      if (c->p_items) cudaFreeHost(c->p_items);
+      c->p_items = nullptr;
+      c->p_items_cap = 0ull;
+      if (cudaMallocHost((void**)&c->p_items, (size_t)total * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return SR_ENOMEM;
+      }
+      c->p_items_cap = total;
+      if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+    }
+    std::vector<int> order((size_t)c->nrep);
+    for (int b = 0; b < c->nrep; ++b) order[(size_t)b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nwin[a] > nwin[b]; });
+    std::memset(c->p_ls, 0, (size_t)c->nrep * sizeof(LatState));
+    for (int b = 0; b < c->nrep; ++b) {
+      c->p_ls[b].pend = (unsigned)c->hdesc[b].NR;
+      c->p_ls[b].n = 1u;
+      c->p_ls[b].ts = c->t_c[b];
+    }
+    unsigned long long t = 0ull;
+    for (const int b : order) {
+      if (nwin[b] <= 0) continue;
+      const int nch = (c->hdesc[b].NR + c->lanes - 1) / c->lanes;
+      for (int ch = 0; ch < nch; ++ch, ++t) c->p_items[t] = task_item(0u, (unsigned)b, (unsigned)ch, t);
+    }
+    *c->p_tail = total;
+    *c->p_active = active;
+    c->async_tail = total;
+    c->async_active = active;
+  }
+  const KParams k = make_params(c);
+  if (!c->gexec || c->g_total != total || std::memcmp(&k, &c->gk, sizeof k) != 0) {
+    const int rc = capture_launch(c, k, total);
+    if (rc != SR_OK) return rc;
+  }
+  if (c->ev_relax[0] && cudaEventRecord(c->ev_relax[0], c->stream) != cudaSuccess) return SR_ECUDA;
+  if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SR_ECUDA;
+  }
+  if (c->ev_relax[1] && cudaEventRecord(c->ev_relax[1], c->stream) != cudaSuccess) return SR_ECUDA;
+  c->launches += 1;
+  c->graph_launches += 1;
+  int rc = cuda_rc(cudaStreamSynchronize(c->stream));
+  if (rc == SR_OK && c->ev_relax[0]) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->ev_relax[0], c->ev_relax[1]) != cudaSuccess) return SR_ECUDA;
+    c->relax_ms += (double)ms;
+    c->relax_launches += 1;
+  }
+  return rc;
+}
+
 // One persistent launch running, for each lattice b, nwin[b] windows of
 // length Tw[b] from its committed time.
 int launch_relax(sr_ctx* c, const double* Tw, const int* nwin) {
@@ -441,6 +629,7 @@ void free_all(sr_ctx* c) {
   if (c->h_rs) cudaFreeHost(c->h_rs);
   if (c->h_obs_i) cudaFreeHost(c->h_obs_i);
   if (c->h_obs_f) cudaFreeHost(c->h_obs_f);
+  free_graph(c);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   for (cudaEvent_t ev : c->ev_relax)
     if (ev) cudaEventDestroy(ev);
@@ -784,7 +973,7 @@ int run_all(sr_ctx* c, const double* Tw, const int* nwin) {
   c->last_nwin = 0;
   rc = SR_OK;
   while (total_left > 0) {
-    rc = launch_relax(c, Tw, left);
+    rc = c->use_graph ? launch_relax_graph(c, Tw, left) : launch_relax(c, Tw, left);
     if (rc != SR_OK) break;
     total_left = 0;
     for (int b = 0; b < c->nrep; ++b) {
@@ -1192,6 +1381,36 @@ int sr_run_window(sr_ctx* c, double t0, double Tw) { return sr_run_windows(c, t0
 int sr_run_batch(sr_ctx* c, const double* Tw, const int* n_windows) {
   if (!c || !Tw || !n_windows) return SR_EINVAL;
   return run_all(c, Tw, n_windows);
+}
+
+int sr_set_graph_launch(sr_ctx* c, int on) {
+  if (!c) return SR_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SR_ECUDA;
+  if (!on) {
+    free_graph(c);
+    c->use_graph = false;
+    return SR_OK;
+  }
+  if (c->use_graph) return SR_OK;
+  const size_t n = (size_t)c->nrep;
+  if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&c->p_desc, n * sizeof(RepDesc)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->p_ls, n * sizeof(LatState)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->p_tail, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->p_active, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    free_graph(c);
+    return SR_ENOMEM;
+  }
+  c->use_graph = true;
+  return SR_OK;
+}
+
+int sr_get_graph_stats(sr_ctx* c, unsigned long long* captures, unsigned long long* replays) {
+  if (!c) return SR_EINVAL;
+  if (captures) *captures = c->graph_captures;
+  if (replays) *replays = c->graph_launches;
+  return SR_OK;
 }
 
 int sr_observables(sr_ctx* c, sr_obs* out) {
