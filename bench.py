@@ -68,13 +68,21 @@ FP64_SLOTS_PER_EVENT = 32 + 2 * 8.6
 HIST_BYTES_PER_BOUNDARY_EVENT = 9 * 2
 HBM_GBS_FALLBACK = 6800.0
 # DRAM bytes (read + write) per relaxation launch of the batched step, mean
-# over the launches of one whole step (one ncu capture on a GB300; the
-# configuration and command are in profiles/); valid only for the kernel
-# sources they were taken on (hash below) and for the same tuning.
-BATCH_TRAFFIC = None            # {"bytes_per_launch": B, "tuning": [W, H, lpw, kappa]}
-BATCH_TRAFFIC_SHA = None
-PLAIN_TRAFFIC = None            # {Tw: bytes per launch} of the L = 1024 launches
-PLAIN_TRAFFIC_SHA = None
+# over the 100 launches of one whole step (one ncu capture on a GB300 of
+#   python bench.py --profile-batch --windows 0 --tune-in TUNE, with
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:relax_kernel --csv
+# and TUNE the autotuner's choice of the same GPU call); valid only for the
+# kernel sources they were taken on (hash below) and for the same tuning
+# (region shape counts, lanes per warp, kappa).
+BATCH_TRAFFIC = {"bytes_per_launch": 14160895882,
+                 "tuning": [{"32x16": 127, "32x32": 107, "16x16": 22}, 0, 8.0]}
+BATCH_TRAFFIC_SHA = "d591b8aed2c2172c"
+# DRAM bytes per launch of the L = 1024 launches, one per window length
+#   python bench.py --profile-case --tw TW --windows 100/TW under the same ncu
+#   metrics with -s 3 -c 1
+PLAIN_TRAFFIC = {0.25: 8675840, 1.0: 107309312, 4.0: 1296592128}
+PLAIN_TRAFFIC_SHA = "d591b8aed2c2172c"
 
 
 def _kernel_sources_sha():

@@ -276,7 +276,8 @@ int sr_run_batch_adaptive(sr_ctx* ctx, const double* t_end, const sr_adapt* opts
  * spins (the coarsened configurations of a long run, not the first quench
  * from the initial spins), runs the adaptive runner with one launch per
  * t_trial, untimed to t_trial (the window lengths settle), then timed to
- * 3 t_trial, and scores committed flips per second.  One
+ * 3 t_trial, and scores committed flips per second; a candidate replaces
+ * the best so far only when it scores at least 2% higher.  One
  * coordinate at a time:
  *   1. one shape for every lattice, among 8x8, 16x8, 16x16, 32x16 and 32x32;
  *   2. a shape per lattice: the largest of those shapes (dividing L_b) with

@@ -1679,8 +1679,12 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
   };
   double best = -1.0, bk = 8.0, bthr = 0.0;
   int blpw = 0;
+  // a candidate replaces the best so far only when it scores 2% higher (the
+  // trials are short host-timed runs; near-ties are left to the earlier
+  // candidate instead of to timing noise)
+  const double margin = 1.02;
   auto keep = [&](double sc) {
-    if (sc <= best) return false;
+    if (best >= 0.0 && sc <= margin * best) return false;
     best = sc;
     best_w = sw;
     best_h = sh;
@@ -1758,7 +1762,7 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
     sh = best_h;
     double sc = 0.0;
     rc = trial(0, kappas[i], &sc);
-    if (rc == SR_OK && sc > best) {
+    if (rc == SR_OK && sc > margin * best) {
       best = sc;
       bk = kappas[i];
     }
@@ -1769,7 +1773,7 @@ int sr_autotune(const sr_replica* reps, int n, const sr_params* common, double t
     sh = best_h;
     double sc = 0.0;
     rc = trial(lpws[i], bk, &sc);
-    if (rc == SR_OK && sc > best) {
+    if (rc == SR_OK && sc > margin * best) {
       best = sc;
       blpw = lpws[i];
     }

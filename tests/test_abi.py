@@ -59,3 +59,12 @@ def test_product_raises_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(OSError):
         sr.library(build_if_missing=False)
+
+
+def test_graph_launch_calls_reject_a_null_context_without_gpu():
+    import paper_cs_0405053_gb300 as sr
+    lib = sr.library()
+    a, b = ctypes.c_ulonglong(7), ctypes.c_ulonglong(7)
+    assert lib.sr_set_graph_launch(None, 1) == sr.SR_EINVAL
+    assert lib.sr_get_graph_stats(None, ctypes.byref(a), ctypes.byref(b)) == sr.SR_EINVAL
+    assert (a.value, b.value) == (7, 7)
