@@ -68,3 +68,38 @@ def test_graph_launch_calls_reject_a_null_context_without_gpu():
     assert lib.sr_set_graph_launch(None, 1) == sr.SR_EINVAL
     assert lib.sr_get_graph_stats(None, ctypes.byref(a), ctypes.byref(b)) == sr.SR_EINVAL
     assert (a.value, b.value) == (7, 7)
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include "sr.h"
+int main(void) {
+  sr_ctx* ctx = NULL;
+  sr_obs o;
+  int rc = sr_create(&ctx, 64, 1.0, 0.05, 1.5, 16, 16, 1);
+  if (rc != SR_OK) { printf("%s\n", sr_strerror(rc)); return 1; }
+  rc = sr_run_window(ctx, 0.0, 1.0);
+  if (rc == SR_OK) rc = sr_observables(ctx, &o);
+  sr_destroy(ctx);
+  return rc == SR_OK ? 0 : 1;
+}
+"""
+
+
+def test_header_is_plain_c_and_links_without_gpu(tmp_path):
+    """A C99 caller of the four boundary calls compiles against include/sr.h
+    with every warning an error, and links against libsr (it is not run)."""
+    import shutil
+    import subprocess
+    from paper_cs_0405053_gb300 import _build
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib = _build.build()
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", os.path.dirname(lib), "-lsr"], check=True)
+    assert exe.exists()
